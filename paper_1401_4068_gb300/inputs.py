@@ -1,0 +1,288 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle and the benchmark.
+
+This module only makes data: the coupled processes that stand in for the paper's simulations
+and MEG recordings, the random trial permutations that define surrogate data sets, and the
+bookkeeping of which (series, analysis time point, surrogate) estimates a workload contains.
+It holds none of the estimator's arithmetic (no embedding, no distances, no counts, no digamma).
+
+Shapes follow the paper's problem statement: a series is trials x samples (``[R][T]``,
+row-major float32), the same layout for source X and target Y (Eq. 3 / Eq. 4 notation:
+repetition r, time t).  Surrogates pair target trial r with source trial ``perms[s][r]``; this
+is the trial shuffling of Fig. 3 expressed on the source side (TE depends only on the pairing).
+
+All generators draw from ``numpy.random.default_rng(seed)`` (PCG64), run the recursions in
+float64, drop ``burn`` leading samples per trial and store float32, so that every consumer
+reads identical bits within one run.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+BASE_SEED = 20140728  # publication year/month/day of the paper; seed = BASE_SEED + config id
+BURN_IN = 200
+
+# AR(2) pair used by the stationary / non-stationary / surrogate workloads:
+#   x_t = AX1 x_{t-1} + AX2 x_{t-2} + eta_x
+#   y_t = AY1 y_{t-1} + AY2 y_{t-2} + c(t) x_{t-U_AR} + eta_y
+AR_AX = (0.5, -0.2)
+AR_AY = (0.4, -0.2)
+AR_COUPLING = 0.5
+AR_U = 5
+AR_SIGMA = 1.0
+
+
+@dataclass
+class Series:
+    """One source/target pair: trials x samples arrays plus its embedding parameters."""
+    src: np.ndarray            # float32 [R][T]
+    tgt: np.ndarray            # float32 [R][T]
+    d: int                     # embedding dimension (d_X = d_Y = d)
+    tau: int                   # embedding delay
+    u: int                     # assumed interaction delay
+    perms: Optional[np.ndarray] = None  # int32 [S][R]: surrogate s pairs tgt trial r with src trial perms[s][r]
+
+    @property
+    def R(self) -> int:
+        return int(self.src.shape[0])
+
+    @property
+    def T(self) -> int:
+        return int(self.src.shape[1])
+
+    @property
+    def S(self) -> int:
+        return 0 if self.perms is None else int(self.perms.shape[0])
+
+
+@dataclass
+class Instance:
+    """One estimate: a series, an analysis window [t_start, t_start+window) and a pairing."""
+    series: int
+    t_start: int
+    window: int
+    perm: int = -1             # -1: original pairing; s >= 0: surrogate s of that series
+
+
+@dataclass
+class Workload:
+    name: str
+    series: List[Series]
+    instances: List[Instance]
+    k: int = 4
+    # For surrogate-test workloads: per series the analysis start points, the window and S.
+    t_starts: Optional[List[List[int]]] = None
+    window: Optional[int] = None
+    S: int = 0
+    notes: str = ""
+    extra: dict = field(default_factory=dict)
+
+    def n_points(self, inst: Instance) -> int:
+        return self.series[inst.series].R * inst.window
+
+    def joint_dim(self, inst: Instance) -> int:
+        return 1 + 2 * self.series[inst.series].d
+
+    def pair_evals(self) -> int:
+        """Ordered (i, j != i) point pairs summed over all instances: the work of ONE pass."""
+        tot = 0
+        for inst in self.instances:
+            n = self.n_points(inst)
+            tot += n * (n - 1)
+        return tot
+
+    def lane_ops(self) -> int:
+        """Algorithmic FP32 operations of ONE pass: D subtractions + D abs-max per ordered pair."""
+        tot = 0
+        for inst in self.instances:
+            n = self.n_points(inst)
+            tot += n * (n - 1) * 2 * self.joint_dim(inst)
+        return tot
+
+
+# ----------------------------------------------------------------------------------------
+# process generators
+# ----------------------------------------------------------------------------------------
+
+def ar2_pair(rng: np.random.Generator, R: int, T: int, coupling_start: Optional[int] = 0,
+             coupling: float = AR_COUPLING, burn: int = BURN_IN):
+    """Unidirectionally coupled AR(2) pair X -> Y with delay AR_U and unit Gaussian noise.
+
+    ``coupling_start``: kept-sample index from which the coupling is on (None: never on).
+    """
+    L = T + burn
+    ex = rng.standard_normal((R, L)) * AR_SIGMA
+    ey = rng.standard_normal((R, L)) * AR_SIGMA
+    x = np.zeros((R, L))
+    y = np.zeros((R, L))
+    for t in range(L):
+        xt = ex[:, t].copy()
+        yt = ey[:, t].copy()
+        if t >= 1:
+            xt += AR_AX[0] * x[:, t - 1]
+            yt += AR_AY[0] * y[:, t - 1]
+        if t >= 2:
+            xt += AR_AX[1] * x[:, t - 2]
+            yt += AR_AY[1] * y[:, t - 2]
+        kept = t - burn
+        if coupling_start is not None and kept >= coupling_start and t >= AR_U:
+            yt += coupling * x[:, t - AR_U]
+        x[:, t] = xt
+        y[:, t] = yt
+    return (np.ascontiguousarray(x[:, burn:], dtype=np.float32),
+            np.ascontiguousarray(y[:, burn:], dtype=np.float32))
+
+
+def pink_noise(rng: np.random.Generator, R: int, L: int) -> np.ndarray:
+    """1/f noise per trial by spectral shaping of white Gaussian noise, unit variance."""
+    w = rng.standard_normal((R, L))
+    f = np.fft.rfft(w, axis=1)
+    freqs = np.arange(f.shape[1], dtype=np.float64)
+    scale = np.zeros_like(freqs)
+    scale[1:] = 1.0 / np.sqrt(freqs[1:])
+    p = np.fft.irfft(f * scale[None, :], n=L, axis=1)
+    p -= p.mean(axis=1, keepdims=True)
+    p /= p.std(axis=1, keepdims=True)
+    return p
+
+
+def pink_pair(rng: np.random.Generator, R: int, T: int, u: int, coupling: float = 0.5,
+              burn: int = BURN_IN):
+    """MEG-like pair: y = pink_y + coupling * x(t-u), x pink, both unit variance before mixing."""
+    L = T + burn
+    x = pink_noise(rng, R, L)
+    yp = pink_noise(rng, R, L)
+    y = yp.copy()
+    y[:, u:] += coupling * x[:, :-u]
+    return (np.ascontiguousarray(x[:, burn:], dtype=np.float32),
+            np.ascontiguousarray(y[:, burn:], dtype=np.float32))
+
+
+def logistic_ar_pair(rng: np.random.Generator, R: int, T: int, u: int = 5, r_log: float = 3.9,
+                     a_y: float = 0.4, coupling: float = 0.5, burn: int = BURN_IN):
+    """Logistic-map source (r = 3.9, x0 ~ U(0.1, 0.9)) driving a noisy AR(1) target
+    through a squared (nonlinear) coupling: y_t = a_y y_{t-1} + coupling * x_{t-u}^2 + eta."""
+    L = T + burn
+    x = np.zeros((R, L))
+    x[:, 0] = rng.uniform(0.1, 0.9, size=R)
+    for t in range(1, L):
+        x[:, t] = r_log * x[:, t - 1] * (1.0 - x[:, t - 1])
+    ey = rng.standard_normal((R, L))
+    y = np.zeros((R, L))
+    for t in range(L):
+        yt = ey[:, t].copy()
+        if t >= 1:
+            yt += a_y * y[:, t - 1]
+        if t >= u:
+            yt += coupling * x[:, t - u] ** 2
+        y[:, t] = yt
+    return (np.ascontiguousarray(x[:, burn:], dtype=np.float32),
+            np.ascontiguousarray(y[:, burn:], dtype=np.float32))
+
+
+def gaussian_pair_iid(rng: np.random.Generator, R: int, T: int, rho: float):
+    """i.i.d. bivariate Gaussian samples (correlation rho) laid out as trials x samples;
+    used for the mutual-information special case of the estimator."""
+    z1 = rng.standard_normal((R, T))
+    z2 = rng.standard_normal((R, T))
+    x = z1
+    y = rho * z1 + np.sqrt(1.0 - rho * rho) * z2
+    return x.astype(np.float32), y.astype(np.float32)
+
+
+def permutations(rng: np.random.Generator, S: int, R: int) -> np.ndarray:
+    """S uniform random permutations of 0..R-1 (surrogate trial pairings), int32 [S][R]."""
+    out = np.empty((S, R), dtype=np.int32)
+    for s in range(S):
+        out[s] = rng.permutation(R).astype(np.int32)
+    return out
+
+
+# ----------------------------------------------------------------------------------------
+# the five workloads
+# ----------------------------------------------------------------------------------------
+
+def _surrogate_instances(n_series_t: Sequence[Sequence[int]], window: int, S: int) -> List[Instance]:
+    insts = []
+    for si, ts in enumerate(n_series_t):
+        for t in ts:
+            insts.append(Instance(si, t, window, -1))
+            for s in range(S):
+                insts.append(Instance(si, t, window, s))
+    return insts
+
+
+def config(cid: int, *, n_t: Optional[int] = None, S: Optional[int] = None,
+           R: Optional[int] = None, n_pairs: Optional[int] = None) -> Workload:
+    """The five benchmark workloads.  Keyword overrides shrink a workload (fewer time points,
+    surrogates, trials or channel pairs) for tests; the defaults are the full sizes."""
+    rng = np.random.default_rng(BASE_SEED + cid)
+    if cid == 1:
+        # AR(2) X->Y, 200 trials x 300 samples, d=2, tau=1, u=5, one window of 5 samples
+        Rr = R or 200
+        src, tgt = ar2_pair(rng, Rr, 300, coupling_start=0)
+        s = Series(src, tgt, d=2, tau=1, u=AR_U)
+        return Workload("C1 stationary AR(2), 1000 points x 5-D, 1 estimate", [s],
+                        [Instance(0, 100, 5, -1)], k=4)
+    if cid == 2:
+        # coupling switched on at sample 500; 100 analysis points, window 3, d=3, tau=2
+        Rr = R or 500
+        src, tgt = ar2_pair(rng, Rr, 1000, coupling_start=500)
+        s = Series(src, tgt, d=3, tau=2, u=AR_U)
+        nt = n_t or 100
+        ts = [9 + 9 * j for j in range(nt)]
+        return Workload("C2 non-stationary AR(2), 1500 points x 7-D, 100 time points", [s],
+                        [Instance(0, t, 3, -1) for t in ts], k=4, t_starts=[ts], window=3)
+    if cid == 3:
+        # surrogate test: 400 trials, d=3, tau=1, window 3, 50 time points x (1 + 1000)
+        Rr = R or 400
+        src, tgt = ar2_pair(rng, Rr, 1000, coupling_start=0)
+        SS = 1000 if S is None else S
+        perms = permutations(rng, SS, Rr)
+        s = Series(src, tgt, d=3, tau=1, u=AR_U, perms=perms)
+        nt = n_t or 50
+        ts = [9 + 18 * j for j in range(nt)]
+        return Workload("C3 surrogate test, 1200 points x 7-D, 50 t x (1+1000)", [s],
+                        _surrogate_instances([ts], 3, SS), k=4, t_starts=[ts], window=3, S=SS)
+    if cid == 4:
+        # 20 pink-noise channel pairs with uneven trials / dims / windows, 30 time points each
+        npairs = n_pairs or 20
+        series, insts = [], []
+        nt = n_t or 30
+        for p in range(npairs):
+            Rp = int(rng.integers(50, 2001)) if R is None else R
+            dp = int(rng.integers(1, 6))
+            Wp = int(rng.integers(1, 6))
+            up = int(rng.integers(2, 21))
+            src, tgt = pink_pair(rng, Rp, 600, up)
+            series.append(Series(src, tgt, d=dp, tau=1, u=up))
+            for j in range(nt):
+                insts.append(Instance(p, 24 + 18 * j, Wp, -1))
+        return Workload("C4 uneven MEG-like batch, 20 pairs x 30 t, N 50..10000, D 3..11",
+                        series, insts, k=4)
+    if cid == 5:
+        # 4000 trials, d=5, window 3 -> 12000 points x 11-D; 200 t x (1 + 200)
+        Rr = R or 4000
+        src, tgt = logistic_ar_pair(rng, Rr, 400, u=5)
+        SS = 200 if S is None else S
+        perms = permutations(rng, SS, Rr)
+        s = Series(src, tgt, d=5, tau=1, u=5, perms=perms)
+        nt = n_t or 200
+        ts = [9 + j for j in range(nt)]
+        return Workload("C5 large ensemble, 12000 points x 11-D, 200 t x (1+200)", [s],
+                        _surrogate_instances([ts], 3, SS), k=4, t_starts=[ts], window=3, S=SS)
+    raise ValueError(f"unknown config {cid}")
+
+
+def sample_instances(w: Workload, n: int, seed: int = 0) -> List[int]:
+    """Indices of a seeded, cost-stratified subset of a workload's instances."""
+    rng = np.random.default_rng(BASE_SEED + 1000 + seed)
+    idx = np.arange(len(w.instances))
+    if n >= len(idx):
+        return list(idx)
+    cost = np.array([w.n_points(i) ** 2 * w.joint_dim(i) for i in w.instances], dtype=np.float64)
+    order = idx[np.argsort(cost, kind="stable")]
+    strata = np.array_split(order, n)
+    return sorted(int(rng.choice(s)) for s in strata if len(s))
