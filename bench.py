@@ -1,0 +1,463 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 ensemble transfer-entropy hot path.
+
+One step = one pass of the whole hot path (embedding gather, max-norm kNN search, marginal
+range counts, digamma sum, surrogate p-values) over one batch of synthetic input.  The default
+workload is the batched surrogate test: 400 trials of a coupled AR(2) pair, d = 3, tau = 1,
+u = 5, window 3 (N = 1200 points in a 7-D joint space), 50 analysis time points x (1 original
++ 1000 trial-shuffled surrogates) = 50,050 estimates, k = 4.
+
+Printed (rank 0, one JSON line): combined max-norm pair evaluations per second (both passes,
+ordered pairs i != j) over all ranks, TE estimates per second, the end-to-end rate through the
+public API with host buffers, the per-instance-launch rate on the same GPU, the roofline of the
+persistent kernel against the FP32 ALU peak, the SM clocks seen, and the CPU oracle timed on a
+bounded sample of the same workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload c3]
+Under torchrun (N > 1) every rank runs the full workload on its own GPU (weak scaling, no
+collective on the data path); value = all ranks' pair evaluations / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "max-norm pair evals/s & TE estimates/s (incl. surrogates), batched vs per-launch"
+FLUSH_BYTES = 256 << 20          # > 129 MB L2: written between timed steps
+FALLBACK_SM_MHZ = 2070.0
+ALU_LANES_PER_SM = 128           # FP32 lanes per SM (4 SMSPs x 32)
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "batched_kernel_traffic.json")
+
+WORKLOADS = {
+    "c3": dict(cid=3, kw={}, desc="C3 surrogate test: AR(2) X->Y, 400 trials, d=3, tau=1, u=5, W=3 "
+               "(N=1200, D=7), 50 time points x (1+1000 surrogates) = 50,050 estimates, k=4"),
+    "c3-small": dict(cid=3, kw=dict(n_t=4, S=200), desc="C3 shapes, 4 time points x (1+200)"),
+    "c1": dict(cid=1, kw={}, desc="C1 stationary AR(2): N=1000, D=5, 1 estimate, k=4"),
+    "c2": dict(cid=2, kw={}, desc="C2 non-stationary AR(2): N=1500, D=7, 100 time points, k=4"),
+    "c4": dict(cid=4, kw={}, desc="C4 uneven MEG-like batch: 20 pink-noise pairs x 30 t, N 50..10000, D 3..11"),
+    "c5": dict(cid=5, kw={}, desc="C5 large ensemble: N=12000, D=11, 200 t x (1+200) = 40,200 estimates"),
+    "c5-small": dict(cid=5, kw=dict(n_t=2, S=20), desc="C5 shapes, 2 time points x (1+20)"),
+}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def pair_evals(w):
+    """Ordered pairs i != j of ONE pass, summed over instances."""
+    return sum(w.n_points(i) * (w.n_points(i) - 1) for i in w.instances)
+
+
+def lane_ops(w):
+    """Algorithmic FP32 operations of both passes: D subtractions + D abs-max per ordered pair."""
+    return 2 * sum(w.n_points(i) * (w.n_points(i) - 1) * 2 * w.joint_dim(i) for i in w.instances)
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1401_4068_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def traffic_per_launch(w):
+    """DRAM bytes of one persistent-kernel launch from the committed ncu summary (a smaller
+    capture of the same instance shape, scaled by the number of estimates, since every estimate
+    stages the same points), or None when absent, taken on another instance shape, or taken on
+    different kernel sources."""
+    try:
+        with open(PROFILE_TRAFFIC) as f:
+            prof = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if prof.get("kernel_src_hash") != kernel_source_hash():
+        return None
+    shape = sorted({(w.n_points(i), w.joint_dim(i)) for i in w.instances})
+    if [list(x) for x in shape] != prof.get("instance_shapes"):
+        return None
+    return prof["dram_bytes"] / prof["estimates"] * len(w.instances)
+
+
+def run_oracle_sample(w, idx, threads):
+    import oracle  # CPU baseline only
+    insts = [w.instances[i] for i in idx]
+    t0 = time.perf_counter()
+    oracle.te_batch(w.series, insts, w.k, n_threads=threads)
+    dt = time.perf_counter() - t0
+    pe = sum(w.n_points(i) * (w.n_points(i) - 1) for i in insts) * 2
+    return pe, dt, len(insts)
+
+
+def cpu_baseline(w, seconds: float):
+    """Oracle as it stands on the host cores, on a bounded sample sized to ~`seconds`."""
+    import oracle
+    from paper_1401_4068_gb300 import inputs as I
+    threads = oracle.default_threads()
+    n = max(threads, 8)
+    idx = I.sample_instances(w, n, seed=11)
+    pe, dt, m = run_oracle_sample(w, idx, threads)
+    if dt < seconds / 3:
+        scale = min(64.0, seconds / max(dt, 1e-3))
+        n2 = min(len(w.instances), int(n * scale))
+        idx = I.sample_instances(w, n2, seed=12)
+        pe, dt, m = run_oracle_sample(w, idx, threads)
+    return {"value": pe / dt, "unit": "pair-evals/s", "cores": threads, "kind": "oracle",
+            "seconds": round(dt, 2), "te_estimates_per_s": m / dt,
+            "sample": f"{m} of {len(w.instances)} estimates (cost-stratified, seeded), both passes"}
+
+
+# ---------------------------------------------------------------------------------- ours
+def bench_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1401_4068_gb300 import build
+    from paper_1401_4068_gb300 import inputs as I
+    from paper_1401_4068_gb300 import te
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    build.build()
+    spec = WORKLOADS[args.workload]
+    w = I.config(spec["cid"], **spec["kw"])
+    surrogate = w.S > 0 and w.t_starts is not None
+    h = te.Handle(local)
+    ds = te.to_device(w.series, dev)
+    te.te_set_profiling(h, True)
+
+    def step(series_dev, outs=None):
+        if surrogate:
+            return te.te_surrogate_test(h, series_dev, w.t_starts[0], w.window, w.S, w.k, out=outs)
+        return te.te_estimate(h, series_dev, w.instances, w.k, te=outs)
+
+    outs = None
+    if surrogate:
+        nt = len(w.t_starts[0])
+        outs = {"te_orig": torch.empty((1, nt), dtype=torch.float64, device=dev),
+                "te_surr": torch.empty((1, nt, w.S), dtype=torch.float64, device=dev),
+                "p": torch.empty((1, nt), dtype=torch.float64, device=dev)}
+    else:
+        outs = torch.empty(len(w.instances), dtype=torch.float64, device=dev)
+
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        step(ds, outs)
+    torch.cuda.synchronize()
+    te.te_sync_status(h)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    sampler = ClockSampler(f"GPU-{uuid}" if uuid else None)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kernel_ms = []
+    launches = 0
+    for a, b in ev:
+        flush.zero_()
+        a.record()
+        step(ds, outs)
+        b.record()
+        launches += te.te_last_launch_count(h)
+        kernel_ms.append(te.te_last_kernel_ms(h))
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    te.te_sync_status(h)
+
+    pe_step = 2 * pair_evals(w)
+    n_est = len(w.instances)
+    value = ws * pe_step * args.steps / (total_ms / 1e3)
+    te_rate = ws * n_est * args.steps / (total_ms / 1e3)
+
+    # ---- roofline of the persistent kernel (CUDA events on its own stream, live)
+    kms = statistics.mean(kernel_ms)
+    ops = lane_ops(w)
+    achieved = ops / (kms / 1e3) / 1e12
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or FALLBACK_SM_MHZ)
+    n_sm = props.multi_processor_count
+    peak = n_sm * ALU_LANES_PER_SM * sm_max * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4),
+            "peak_source": f"{n_sm} SMs x {ALU_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
+                           f"({'MEASURED_PEAKS.json sm_max_mhz' if peaks.get('sm_max_mhz') else 'fallback clock'})",
+            "op": "FP32 subtract or abs-max; 2*D per ordered pair per pass, 2 passes",
+            "kernel": "batched_kernel", "kernel_ms": round(kms, 4),
+            "traffic": traffic_per_launch(w)}
+    if clocks.get("sm_mhz"):
+        roof["frac_at_sampled_clock"] = round(achieved / (n_sm * ALU_LANES_PER_SM * clocks["sm_mhz"] * 1e6 / 1e12), 4)
+
+    # ---- end to end through the public API: pinned host inputs in, results out, every step
+    import torch as _t
+    host = []
+    for s in w.series:
+        hs = {"src": _t.from_numpy(np.ascontiguousarray(s.src)).pin_memory(),
+              "tgt": _t.from_numpy(np.ascontiguousarray(s.tgt)).pin_memory(),
+              "perms": None if s.perms is None else _t.from_numpy(np.ascontiguousarray(s.perms)).pin_memory()}
+        host.append(hs)
+    h2d = sum(v.numel() * v.element_size() for hs in host for v in hs.values() if v is not None)
+    if surrogate:
+        out_host = {k: _t.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in outs.items()}
+    else:
+        out_host = _t.empty(outs.shape, dtype=outs.dtype).pin_memory()
+    d2h = (sum(v.numel() * v.element_size() for v in out_host.values()) if surrogate
+           else out_host.numel() * out_host.element_size())
+
+    def e2e_step():
+        for s, hs in zip(ds, host):
+            s.src.copy_(hs["src"], non_blocking=True)
+            s.tgt.copy_(hs["tgt"], non_blocking=True)
+            if hs["perms"] is not None:
+                s.perms.copy_(hs["perms"], non_blocking=True)
+        step(ds, outs)
+        if surrogate:
+            for k in outs:
+                out_host[k].copy_(outs[k], non_blocking=True)
+        else:
+            out_host.copy_(outs, non_blocking=True)
+
+    e2e_steps = max(3, args.steps // 2)
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    eev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
+    for a, b in eev:
+        flush.zero_()
+        a.record()
+        e2e_step()
+        b.record()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in eev)
+    if ws > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": ws * pe_step * e2e_steps / (e2e_ms / 1e3), "unit": "pair-evals/s",
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+           "te_estimates_per_s": ws * n_est * e2e_steps / (e2e_ms / 1e3),
+           "ms_per_step": e2e_ms / e2e_steps}
+
+    # ---- per-instance launches of the same kernel, same GPU and stream, on a sub-batch
+    per = None
+    if not args.no_per_launch:
+        if surrogate:
+            n_t_sub = max(1, min(len(w.t_starts[0]), args.per_launch_instances // (w.S + 1)))
+            wsub = I.Workload(w.name, w.series, w.instances[: n_t_sub * (w.S + 1)], w.k,
+                              [w.t_starts[0][:n_t_sub]], w.window, w.S)
+        else:
+            wsub = I.Workload(w.name, w.series, w.instances[: args.per_launch_instances], w.k)
+
+        def sub_step(o=None):
+            if surrogate:
+                return te.te_surrogate_test(h, ds, wsub.t_starts[0], wsub.window, wsub.S, wsub.k)
+            return te.te_estimate(h, ds, wsub.instances, wsub.k)
+
+        res = {}
+        for mode in (True, False):
+            te.te_set_batching(h, mode)
+            sub_step()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            a.record()
+            sub_step()
+            b.record()
+            torch.cuda.synchronize()
+            res[mode] = a.elapsed_time(b)
+            n_launch = te.te_last_launch_count(h)
+            res[(mode, "launches")] = n_launch
+        te.te_set_batching(h, False)
+        pe_sub = 2 * pair_evals(wsub)
+        per = {"instances": len(wsub.instances),
+               "per_instance_launch": {"value": pe_sub / (res[True] / 1e3), "unit": "pair-evals/s",
+                                       "te_estimates_per_s": len(wsub.instances) / (res[True] / 1e3),
+                                       "ms": round(res[True], 3), "kernel_launches": res[(True, "launches")]},
+               "batched_same_subset": {"value": pe_sub / (res[False] / 1e3), "unit": "pair-evals/s",
+                                       "ms": round(res[False], 3), "kernel_launches": res[(False, "launches")]},
+               }
+        per["batched_vs_per_launch"] = round(res[True] / res[False], 2)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.cpu_seconds)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": spec["desc"], "estimates_per_step": n_est,
+                   "pair_evals_per_step": pe_step, "k": w.k,
+                   "l2": "256 MiB buffer written between timed steps (inputs smaller than L2)",
+                   "per_rank": "every rank runs the full workload (weak scaling)"},
+        "te_estimates_per_s": te_rate,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clocks, "per_launch": per,
+        "batched_vs_per_launch": None if per is None else per["batched_vs_per_launch"],
+        "impl": "ours",
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------------- reference
+def bench_reference(args):
+    """The oracle (plain C, host threads) on the host cores: the reference arm of this tier."""
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1401_4068_gb300 import inputs as I
+    spec = WORKLOADS[args.workload]
+    w = I.config(spec["cid"], **spec["kw"])
+    threads = oracle.default_threads()
+    per_step = max(threads, args.reference_instances)
+    for s in range(args.warmup):
+        run_oracle_sample(w, I.sample_instances(w, threads, seed=100 + s), threads)
+    pe_tot, dt_tot, n_tot = 0, 0.0, 0
+    for s in range(args.steps):
+        pe, dt, m = run_oracle_sample(w, I.sample_instances(w, per_step, seed=200 + s), threads)
+        pe_tot += pe
+        dt_tot += dt
+        n_tot += m
+    value = pe_tot / dt_tot
+    sample = f"{per_step} cost-stratified estimates of {len(w.instances)} per step, both passes"
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt_tot * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": spec["desc"], "estimates_per_step": per_step, "k": w.k},
+        "impl": "reference",
+        "te_estimates_per_s": n_tot / dt_tot,
+        "cpu_baseline": {"value": value, "unit": "pair-evals/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "pair-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c3")
+    ap.add_argument("--per-launch-instances", type=int, default=2002)
+    ap.add_argument("--no-per-launch", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--reference-instances", type=int, default=32)
+    args = ap.parse_args()
+    if args.impl == "ours":
+        args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

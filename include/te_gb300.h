@@ -1,0 +1,185 @@
+/* te_gb300.h - C ABI of the GB300 (sm_103a) ensemble transfer-entropy hot path.
+ *
+ * The library estimates TE_SPO(X -> Y, t, u) with the ensemble KSG estimator of Wollstadt et
+ * al. (PLoS ONE 2014): for every analysis time point and every trial-shuffled surrogate it
+ * builds the delay-embedded joint space (y_t, y-, x-) (Eq. 6, Eq. 7, Eq. 10), finds every
+ * point's k-th nearest neighbour distance under the maximum norm, counts neighbours strictly
+ * inside that radius in the three marginal spaces and averages the digamma sum of Eq. 9.
+ * All arithmetic runs in the library's CUDA kernels; no call falls back to the CPU.
+ *
+ * Conventions shared by every call
+ *  - Data pointers (series, perms, points, eps, counts, results) are caller-owned DEVICE
+ *    pointers on the handle's device, e.g. torch tensors' data_ptr(). Descriptor arrays
+ *    (te_series, te_instance, t_starts, te_params) are HOST memory, read during the call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL: the legacy default stream). Every call
+ *    is asynchronous on it: results are valid after the stream has been synchronised.
+ *  - Arguments are validated on the host before anything is launched; an invalid call
+ *    returns TE_EINVAL or TE_ERANGE, launches nothing and leaves outputs untouched.
+ *  - Series are trials x samples, float32, row-major: x[r * T + t] (repetition r, time t).
+ *  - Coordinates must be finite. Distances are FP32 (|fl32(p - q)|, round to nearest, no
+ *    flush to zero); neighbour counts are exact integers; TE is returned in FP64 nats.
+ *  - Point layout (te_embed output, te_knn_maxnorm / te_range_count input) is structure of
+ *    arrays: coordinate c of point i at points[c * ld + i], ld >= N, ld a multiple of 4 and
+ *    the base pointer 16-byte aligned. Joint coordinate order: [ y_t | y- (d_y) | x- (d_x) ].
+ *    Points are repetitions concatenated in order: i = r * W + w for window sample w.
+ *  - A handle may be used by one host thread at a time.
+ *  - Errors: TE_ECUDA reports a CUDA runtime error, te_last_error() the message.
+ */
+#ifndef TE_GB300_H
+#define TE_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TE_ABI_VERSION 1
+
+typedef enum te_status {
+    TE_OK = 0,
+    TE_EINVAL = 1,   /* bad argument: null pointer, size, alignment, k, permutation index    */
+    TE_ERANGE = 2,   /* embedding reaches before sample 0 or past sample T-1                   */
+    TE_ENOMEM = 3,   /* device workspace could not be allocated                                */
+    TE_ECUDA = 4,    /* CUDA runtime error (launch or previous asynchronous fault)             */
+    TE_ETIMEOUT = 5, /* reserved: a bounded device wait ran out (no kernel waits today)        */
+    TE_ENOTIMPL = 6  /* size outside what this build supports (see each call's limits)         */
+} te_status;
+
+/* Embedding parameters of one estimate (paper notation):
+ *   d       embedding dimension of target and source past states (Eq. 6 / Eq. 7): 1 <= d <= 5
+ *           for te_estimate / te_surrogate_test, 1 <= d <= 15 for te_embed
+ *   tau     embedding delay in samples (Eq. 6), tau >= 1
+ *   u       assumed interaction delay: the source state is taken at t - u (Eq. 3), u >= 0
+ *   k       number of nearest neighbours in the joint space (Eq. 9), 1 <= k <= 16
+ *   t_start first sample of the analysis window, window = its length W >= 1 (Eq. 10) */
+typedef struct te_params {
+    int32_t d, tau, u, k, t_start, window;
+} te_params;
+
+/* One source/target pair of trial ensembles.
+ *   src, tgt  device float32 [R][T]; perms device int32 [S][R] (NULL when S == 0).
+ *   Surrogate s pairs target repetition r with source repetition perms[s * R + r]; this is
+ *   the repetition shuffling of Fig. 3 (TE depends only on the pairing). Entries must lie in
+ *   0 .. R-1: the kernels clamp an entry outside that range to 0 and raise a device flag that
+ *   te_sync_status() reports as TE_EINVAL. */
+typedef struct te_series {
+    const float* src;
+    const float* tgt;
+    int32_t R, T, d, tau, u, S;
+    const int32_t* perms;
+} te_series;
+
+/* One estimate: series index, analysis window [t_start, t_start + window), pairing
+ * (perm = -1: original repetitions, perm = s >= 0: surrogate s of that series). */
+typedef struct te_instance {
+    int32_t series, t_start, window, perm;
+} te_instance;
+
+typedef struct te_handle te_handle;
+
+/* Create a handle bound to CUDA device `device` (made current during every call). The handle
+ * owns the device workspace (instance tables, work queue, per-item partial sums, the digamma
+ * table), cached plans and CUDA graphs; memory grows on demand and is freed by te_destroy.
+ * Returns TE_EINVAL for a null `out` or a bad device index, TE_ECUDA if the device cannot be
+ * used. */
+te_status te_create(te_handle** out, int32_t device);
+
+/* Free everything the handle owns. Waits for the handle's internal work; NULL is a no-op. */
+void te_destroy(te_handle* h);
+
+/* Message of the last failed call on this handle ("" after success). Valid until the next
+ * call on the handle. A NULL handle returns the message of the last failed te_create. */
+const char* te_last_error(const te_handle* h);
+
+/* Synchronise `stream` and report device-side flags raised since the previous check
+ * (currently: an out-of-range permutation entry -> TE_EINVAL). Clears the flags. */
+te_status te_sync_status(te_handle* h, void* stream);
+
+/* te_embed - delay embedding of one estimate's point set (Eq. 6, Eq. 7, source state at t-u
+ * as in the State space reconstruction paragraph, pooling of Eq. 10).
+ * Point i = r * W + w (t' = t_start + w) gets the D = 1 + 2d coordinates
+ *   [ y_r(t'), y_r(t'-1), y_r(t'-1-tau), ..., y_r(t'-1-(d-1)tau),
+ *     x_s(t'-u), x_s(t'-u-tau), ..., x_s(t'-u-(d-1)tau) ],   s = src_perm ? src_perm[r] : r.
+ *   src, tgt  device [R][T]; src_perm device int32 [R] or NULL (identity).
+ *   points    device output [D][ld], N = R * window, ld >= N, ld % 4 == 0, 16-byte aligned.
+ *   p->k is not used. TE_ERANGE if a touched sample lies outside 0 .. T-1. */
+te_status te_embed(te_handle* h, const float* src, const float* tgt, int32_t R, int32_t T,
+                   const te_params* p, const int32_t* src_perm, float* points, int32_t ld,
+                   void* stream);
+
+/* te_knn_maxnorm - k-th nearest-neighbour distance of every point in the joint space under
+ * the maximum norm, the point itself excluded (kNNS of the Implementation section, "Core
+ * algorithm": brute-force infinity-norm search; the radii of Eq. 9).
+ *   points  device [D][ld] (layout above), 1 <= D <= 32, N >= k + 1, 1 <= k <= 16.
+ *   eps     device float32 [N] output: eps[i] = k-th smallest of max_c |fl32(p_ic - p_jc)|,
+ *           j != i (exact: equal to the FP32 value a sequential search computes).
+ *   nn      device int32 [N][k] output or NULL: the k nearest indices in (distance, index)
+ *           order, ties to the lower index. */
+te_status te_knn_maxnorm(te_handle* h, const float* points, int32_t N, int32_t D, int32_t ld,
+                         int32_t k, float* eps, int32_t* nn, void* stream);
+
+/* te_range_count - neighbour counts strictly inside eps[i] in the three marginal spaces of
+ * Eq. 9 (range search of the Implementation section), the point itself excluded:
+ *   counts[0*N + i] = n_z  : #{ j != i : max over y- coords          < eps[i] }
+ *   counts[1*N + i] = n_yz : #{ j != i : max over (y_t, y-) coords   < eps[i] }
+ *   counts[2*N + i] = n_xz : #{ j != i : max over (y-, x-) coords    < eps[i] }
+ *   points  device [D][ld], D = 1 + d_y + d_x <= 32, d_y >= 0, d_x >= 0, N >= 1.
+ *   eps     device float32 [N] (typically te_knn_maxnorm's output).
+ *   counts  device int32 [3][N] output. */
+te_status te_range_count(te_handle* h, const float* points, int32_t N, int32_t d_y, int32_t d_x,
+                         int32_t ld, const float* eps, int32_t* counts, void* stream);
+
+/* te_estimate - TE of many estimates in one batched launch (Eq. 9 / Eq. 10 for each instance):
+ * embedding, kNN search, range counts and the digamma sum of every instance run in one
+ * persistent kernel that takes (instance, query tile) work items from a device queue, followed
+ * by one finalisation kernel; the pair of launches is captured once per argument signature in
+ * a CUDA graph and replayed. Instances may mix R, d, W and series.
+ *   series   host array [n_series]; inst host array [n_inst], N_i = R * window >= k + 1.
+ *   te       device float64 [n_inst] output: psi(k) + mean_i(psi(n_z+1) - psi(n_yz+1)
+ *            - psi(n_xz+1)). Per-point digamma terms are summed in compensated FP32
+ *            (float-float), per-item partials and the mean in FP64.
+ *   err_bound device float64 [n_inst] or NULL: a bound on |te - exact-arithmetic value of
+ *            the same counts| from that summation.
+ *   counts   device int32 or NULL: per instance its [3][N_i] block, blocks concatenated in
+ *            instance order.   eps: device float32 or NULL: per instance [N_i], concatenated.
+ * Limits: N_i <= 65536, 1 <= d <= 5, k <= 16 (TE_ENOTIMPL beyond). */
+te_status te_estimate(te_handle* h, const te_series* series, int32_t n_series,
+                      const te_instance* inst, int32_t n_inst, int32_t k, double* te,
+                      double* err_bound, int32_t* counts, float* eps, void* stream);
+
+/* te_surrogate_test - the surrogate test of the paper ("TE calculation and statistical testing
+ * against surrogate data", Fig. 2 steps 2-6): for every series and every analysis start
+ * t_starts[j], the original estimate and S surrogates (perms[0 .. S-1] of the series), all in
+ * one batched launch as te_estimate, then p = #{s : TE_s >= TE_0} / S.
+ *   te_orig device float64 [n_series][n_t]; te_surr device float64 [n_series][n_t][S];
+ *   p       device float64 [n_series][n_t] (NaN when S == 0). Every series needs S <= its S. */
+te_status te_surrogate_test(te_handle* h, const te_series* series, int32_t n_series,
+                            const int32_t* t_starts, int32_t n_t, int32_t window, int32_t S,
+                            int32_t k, double* te_orig, double* te_surr, double* p, void* stream);
+
+/* Measurement hooks (no effect on results).
+ * te_set_profiling(h, 1) makes te_estimate / te_surrogate_test record CUDA events around the
+ * persistent kernel on the call's stream; te_last_kernel_ms() synchronises on the stop event
+ * and returns that kernel's duration. te_last_launch_count() returns how many kernels the
+ * last call launched (graph replays count their kernel nodes). */
+te_status te_set_profiling(te_handle* h, int32_t enable);
+te_status te_last_kernel_ms(te_handle* h, float* ms);
+int32_t te_last_launch_count(const te_handle* h);
+
+/* Launch-configuration control for the batched kernel (used by the autotuner and tests).
+ * threads: CTA size (multiple of 32, 64..512) or 0 for the built-in choice; qpt: queries per
+ * thread (2 or 4) or 0 for automatic. Takes effect on the next te_estimate call. */
+te_status te_set_launch_config(te_handle* h, int32_t threads, int32_t qpt);
+
+/* Batching mode of te_estimate / te_surrogate_test. per_instance = 0 (default): one persistent
+ * launch for the whole batch, captured in a CUDA graph. per_instance = 1: the same kernel and
+ * tables, launched once per instance with a grid of that instance's work items and no graph,
+ * the way an unbatched implementation runs one search space per launch (the comparison of the
+ * Implementation section's "several chunks per launch" design). Results are bit-identical. */
+te_status te_set_batching(te_handle* h, int32_t per_instance);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TE_GB300_H */

@@ -1,0 +1,739 @@
+// Host side of the C ABI declared in te_gb300.h: argument validation, the batch plan
+// (instance table, cost-ordered work items, launch shape), device workspace, the digamma
+// table, CUDA-graph capture/replay and the measurement hooks. All arithmetic of the method
+// runs in the kernels of te_unit.cu / te_batched_*.cu / te_finalize.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "te_internal.h"
+
+#define TE_EXPORT extern "C" __attribute__((visibility("default")))
+
+namespace {
+
+using te::BatchArgs;
+using te::BatchedVariant;
+using te::InstDesc;
+using te::WorkItem;
+
+constexpr int kMaxN = 65536;          // largest point count of one estimate
+constexpr int kMaxK = 16;
+constexpr int kMaxD = 32;             // te_knn_maxnorm / te_range_count
+constexpr int kMaxEmbedDim = 15;      // te_embed: D = 1 + 2d <= 31
+constexpr int kMaxBatchedD = 5;       // te_estimate / te_surrogate_test
+constexpr int kSmemCapBytes = 64 * 1024;  // reference tile budget of the batched kernel
+
+std::string g_create_error;
+
+// digamma at positive integers in FP64: -gamma + H_{n-1} below 16, the asymptotic expansion
+// ln n - 1/(2n) - sum_k B_2k / (2k n^2k) (six terms, error < 1e-16) from 16 on
+double digamma_int(int n) {
+    if (n < 16) {
+        double s = -0.57721566490153286060651209;
+        for (int m = 1; m < n; ++m) s += 1.0 / m;
+        return s;
+    }
+    const double x = n, r2 = 1.0 / (x * x);
+    const double series =
+        r2 * (1.0 / 12 - r2 * (1.0 / 120 - r2 * (1.0 / 252 - r2 * (1.0 / 240 - r2 * (1.0 / 132 - r2 * (691.0 / 32760))))));
+    return std::log(x) - 0.5 / x - series;
+}
+
+template <class T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    cudaError_t ensure(size_t want, bool* grew = nullptr) {
+        if (want <= n) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        size_t cap = std::max<size_t>(want, 64);
+        cudaError_t e = cudaMalloc(&p, cap * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        n = cap;
+        if (grew) *grew = true;
+        return cudaSuccess;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+template <class T>
+struct HostBuf {  // pinned staging for asynchronous uploads
+    T* p = nullptr;
+    size_t n = 0;
+    cudaError_t ensure(size_t want) {
+        if (want <= n) return cudaSuccess;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        n = 0;
+        size_t cap = std::max<size_t>(want, 64);
+        cudaError_t e = cudaMallocHost(&p, cap * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        n = cap;
+        return cudaSuccess;
+    }
+    void release() {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+struct Plan {
+    std::vector<InstDesc> insts;  // caller order
+    std::vector<WorkItem> items;  // cost order, items of an instance contiguous
+    BatchedVariant var{};
+    int threads = 0, grid = 0, smem_floats = 0;
+    size_t smem = 0;
+    double err_coef = 0;
+    int64_t n_points = 0;
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+uint64_t fnv(uint64_t h, const void* data, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(data);
+    for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    return h;
+}
+
+}  // namespace
+
+struct te_handle {
+    int device = 0;
+    int sm_count = 0;
+    std::string err;
+    cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
+    cudaEvent_t upload_done = nullptr;  // guards reuse of the pinned staging buffer
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool profiling = false, ev_recorded = false;
+    int last_launches = 0;
+    int cfg_threads = 0, cfg_qpt = 0;
+    bool per_instance = false;  // one launch per instance instead of one persistent launch
+
+    DevBuf<InstDesc> d_insts;
+    DevBuf<WorkItem> d_items;
+    DevBuf<int32_t> d_words;  // [0] queue head, [1] flags
+    DevBuf<double> d_partial, d_partial_abs, d_te_all;
+    DevBuf<float2> d_psi;
+    HostBuf<unsigned char> h_stage;
+    int workspace_gen = 0;
+
+    uint64_t graph_key = 0;
+    int graph_gen = -1;
+    cudaGraphExec_t graph_exec = nullptr;
+    int graph_launches = 0;
+
+    te_status fail(te_status s, const char* fmt, ...) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        err = buf;
+        return s;
+    }
+    te_status cuda_fail(cudaError_t e, const char* what) {
+        return fail(TE_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+    }
+    void drop_graph() {
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        graph_exec = nullptr;
+        graph_key = 0;
+        graph_gen = -1;
+    }
+};
+
+namespace {
+
+te_status ensure_psi(te_handle* h) {
+    if (h->d_psi.n >= (size_t)kMaxN + 2) return TE_OK;
+    bool grew = false;
+    cudaError_t e = h->d_psi.ensure((size_t)kMaxN + 2, &grew);
+    if (e != cudaSuccess) return h->fail(TE_ENOMEM, "digamma table: %s", cudaGetErrorString(e));
+    std::vector<float2> tab((size_t)kMaxN + 2);
+    tab[0] = make_float2(0.f, 0.f);
+    for (int n = 1; n < kMaxN + 2; ++n) {
+        const double v = digamma_int(n);
+        const float hi = (float)v;
+        const float lo = (float)(v - (double)hi);
+        tab[n] = make_float2(hi, lo);
+    }
+    e = cudaMemcpy(h->d_psi.p, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return h->cuda_fail(e, "digamma table upload");
+    ++h->workspace_gen;
+    return TE_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// sample-index range of one estimate: target past reaches t_start-1-(d-1)tau, source past
+// t_start-u-(d-1)tau, the window ends at t_start+W-1
+bool embed_in_range(int T, int d, int tau, int u, int t_start, int W) {
+    if (t_start < 0 || W < 1) return false;
+    if ((int64_t)t_start + W - 1 > (int64_t)T - 1) return false;
+    if ((int64_t)t_start - 1 - (int64_t)(d - 1) * tau < 0) return false;
+    if ((int64_t)t_start - u - (int64_t)(d - 1) * tau < 0) return false;
+    return true;
+}
+
+te_status validate_series(te_handle* h, const te_series* series, int n_series) {
+    if (!series || n_series < 1) return h->fail(TE_EINVAL, "series: null or n_series < 1");
+    for (int s = 0; s < n_series; ++s) {
+        const te_series& S = series[s];
+        if (!S.src || !S.tgt) return h->fail(TE_EINVAL, "series %d: null src/tgt", s);
+        if (S.R < 1 || S.T < 1) return h->fail(TE_EINVAL, "series %d: R=%d T=%d", s, S.R, S.T);
+        if (S.d < 1 || S.d > kMaxBatchedD)
+            return h->fail(TE_ENOTIMPL, "series %d: d=%d outside 1..%d", s, S.d, kMaxBatchedD);
+        if (S.tau < 1 || S.u < 0) return h->fail(TE_EINVAL, "series %d: tau=%d u=%d", s, S.tau, S.u);
+        if (S.S < 0 || (S.S > 0 && !S.perms))
+            return h->fail(TE_EINVAL, "series %d: S=%d with perms=%p", s, S.S, (const void*)S.perms);
+        if ((int64_t)S.R * S.T > ((int64_t)1 << 40)) return h->fail(TE_EINVAL, "series %d too large", s);
+    }
+    return TE_OK;
+}
+
+// choose CTA size and queries per thread for a batch
+void choose_shape(te_handle* h, const std::vector<InstDesc>& insts, int ks, int* threads, int* qpt) {
+    int q = h->cfg_qpt ? h->cfg_qpt : (ks == 5 ? 4 : 2);
+    if (ks != 5) q = 2;
+    *qpt = q;
+    if (h->cfg_threads) {
+        *threads = h->cfg_threads;
+        return;
+    }
+    bool uniform = true;
+    for (const auto& I : insts) uniform &= (I.N == insts[0].N);
+    if (!uniform) {
+        *threads = 256;
+        return;
+    }
+    // uniform N: fewest padded query slots, then the CTA size nearest 256
+    const int N = insts[0].N;
+    int best_t = 256;
+    int64_t best_slots = INT64_MAX;
+    for (int m = 1; m <= 64; ++m) {
+        int t = 32 * ((N + m * q * 32 - 1) / (m * q * 32));
+        if (t < 64) t = 64;
+        if (t > te::kBatchedMaxThreads) continue;
+        const int64_t per = (int64_t)t * q;
+        const int64_t slots = ((N + per - 1) / per) * per;
+        if (slots < best_slots || (slots == best_slots && std::abs(t - 256) < std::abs(best_t - 256))) {
+            best_slots = slots;
+            best_t = t;
+        }
+        if (t == 64) break;
+    }
+    *threads = best_t;
+}
+
+te_status build_plan(te_handle* h, const te_series* series, int n_series, const te_instance* inst,
+                     int n_inst, int k, Plan* P) {
+    P->insts.resize(n_inst);
+    int dlo = 99, dhi = 0, nmax = 0, dmaxN = 0;
+    int64_t off = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        const te_instance& in = inst[i];
+        if (in.series < 0 || in.series >= n_series)
+            return h->fail(TE_EINVAL, "instance %d: series %d out of range", i, in.series);
+        const te_series& S = series[in.series];
+        if (in.window < 1) return h->fail(TE_EINVAL, "instance %d: window %d", i, in.window);
+        if (in.perm < -1 || in.perm >= S.S)
+            return h->fail(TE_EINVAL, "instance %d: perm %d outside -1..%d", i, in.perm, S.S - 1);
+        const int64_t N = (int64_t)S.R * in.window;
+        if (N > kMaxN) return h->fail(TE_ENOTIMPL, "instance %d: N=%lld > %d", i, (long long)N, kMaxN);
+        if (N < k + 1) return h->fail(TE_EINVAL, "instance %d: N=%lld < k+1=%d", i, (long long)N, k + 1);
+        if (!embed_in_range(S.T, S.d, S.tau, S.u, in.t_start, in.window))
+            return h->fail(TE_ERANGE, "instance %d: t_start=%d window=%d d=%d tau=%d u=%d outside 0..%d", i,
+                           in.t_start, in.window, S.d, S.tau, S.u, S.T - 1);
+        InstDesc& I = P->insts[i];
+        I.src = S.src;
+        I.tgt = S.tgt;
+        I.perm = in.perm >= 0 ? S.perms + (size_t)in.perm * S.R : nullptr;
+        I.R = S.R;
+        I.T = S.T;
+        I.W = in.window;
+        I.t_start = in.t_start;
+        I.tau = S.tau;
+        I.u = S.u;
+        I.d = S.d;
+        I.N = (int)N;
+        I.pt_off = off;
+        off += N;
+        dlo = std::min(dlo, S.d);
+        dhi = std::max(dhi, S.d);
+        nmax = std::max(nmax, (int)N);
+        dmaxN = std::max(dmaxN, (int)(((N + 3) & ~3) * (1 + 2 * S.d)));
+    }
+    P->n_points = off;
+    const int ks = k <= 4 ? 5 : 17;
+    int threads, qpt;
+    choose_shape(h, P->insts, ks, &threads, &qpt);
+    P->var = BatchedVariant{dlo == dhi ? dlo : 1, dlo == dhi ? dhi : 5, ks, qpt};
+    P->threads = threads;
+    // work items: instances in descending cost (N^2 D), items of one instance contiguous
+    std::vector<int> order(n_inst);
+    for (int i = 0; i < n_inst; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const InstDesc &A = P->insts[a], &B = P->insts[b];
+        return (double)A.N * A.N * (1 + 2 * A.d) > (double)B.N * B.N * (1 + 2 * B.d);
+    });
+    const int per = threads * qpt;
+    P->items.clear();
+    int max_items = 1;
+    for (int i : order) {
+        InstDesc& I = P->insts[i];
+        I.item_begin = (int)P->items.size();
+        I.n_items = (I.N + per - 1) / per;
+        max_items = std::max(max_items, I.n_items);
+        for (int m = 0; m < I.n_items; ++m) P->items.push_back(WorkItem{i, m * per});
+    }
+    P->smem_floats = std::min(kSmemCapBytes / 4, dmaxN);
+    P->smem_floats = std::max(P->smem_floats, 4 * 11);
+    P->smem = (size_t)P->smem_floats * sizeof(float);
+    // bound on the summation error relative to sum |terms| (see te_estimate in the header):
+    // 3*qpt float-float additions per thread (<= 2^-46 each), table rounding (2^-47), FP64
+    // reductions over threads and items
+    P->err_coef = 3.0 * qpt * 0x1p-46 + 0x1p-47 + (threads + max_items + 64) * 0x1p-52;
+    const void* fn = te::batched_kernel_ptr(P->var);
+    if (!fn) return h->fail(TE_ENOTIMPL, "no kernel variant for d=%d..%d ks=%d qpt=%d", dlo, dhi, ks, qpt);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smem);
+    if (e != cudaSuccess) return h->cuda_fail(e, "cudaFuncSetAttribute");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, P->smem);
+    if (e != cudaSuccess) return h->cuda_fail(e, "occupancy query");
+    if (per_sm < 1) return h->fail(TE_ENOTIMPL, "batched kernel does not fit: threads=%d smem=%zu", threads, P->smem);
+    P->grid = (int)std::min<int64_t>((int64_t)per_sm * h->sm_count, (int64_t)P->items.size());
+    (void)nmax;
+    return TE_OK;
+}
+
+// Upload the plan's tables (pinned staging -> device on `stream`).
+te_status upload_tables(te_handle* h, const Plan& P, cudaStream_t stream) {
+    const size_t bi = P.insts.size() * sizeof(InstDesc), bt = P.items.size() * sizeof(WorkItem);
+    cudaError_t e;
+    if ((e = cudaEventSynchronize(h->upload_done)) != cudaSuccess) return h->cuda_fail(e, "staging reuse");
+    if ((e = h->h_stage.ensure(bi + bt)) != cudaSuccess) return h->fail(TE_ENOMEM, "pinned staging");
+    std::memcpy(h->h_stage.p, P.insts.data(), bi);
+    std::memcpy(h->h_stage.p + bi, P.items.data(), bt);
+    if ((e = cudaMemcpyAsync(h->d_insts.p, h->h_stage.p, bi, cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(h->d_items.p, h->h_stage.p + bi, bt, cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
+        (e = cudaEventRecord(h->upload_done, stream)) != cudaSuccess)
+        return h->cuda_fail(e, "table upload");
+    return TE_OK;
+}
+
+BatchArgs batch_args(te_handle* h, const Plan& P, int k, int32_t* counts, float* eps) {
+    BatchArgs a{};
+    a.insts = h->d_insts.p;
+    a.items = h->d_items.p;
+    a.n_items = (int)P.items.size();
+    a.queue = h->d_words.p;
+    a.flags = h->d_words.p + 1;
+    a.psi = h->d_psi.p;
+    a.k = k;
+    a.smem_floats = P.smem_floats;
+    a.partial = h->d_partial.p;
+    a.partial_abs = h->d_partial_abs.p;
+    a.counts_out = counts;
+    a.eps_out = eps;
+    return a;
+}
+
+// The unbatched baseline: the same kernel and tables, but one launch per instance (its grid is
+// that instance's work items, its queue counter its own), launched directly without a graph.
+te_status run_per_instance(te_handle* h, const Plan& P, int n_inst, int k, double* te_dst, double* err,
+                           int32_t* counts, float* eps, int n_groups, int S, double* te_orig,
+                           double* te_surr, double* p, cudaStream_t stream) {
+    te_status st = upload_tables(h, P, stream);
+    if (st != TE_OK) return st;
+    h->drop_graph();
+    cudaError_t e = cudaMemsetAsync(h->d_words.p + 2, 0, (size_t)n_inst * sizeof(int32_t), stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "clear queues");
+    const BatchArgs a = batch_args(h, P, k, counts, eps);
+    int launches = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        const InstDesc& I = P.insts[i];
+        BatchArgs ai = a;
+        ai.items = a.items + I.item_begin;
+        ai.n_items = I.n_items;
+        ai.queue = h->d_words.p + 2 + i;
+        ai.partial = a.partial + I.item_begin;
+        ai.partial_abs = a.partial_abs + I.item_begin;
+        if (h->profiling && i == 0 && (e = cudaEventRecord(h->ev0, stream)) != cudaSuccess)
+            return h->cuda_fail(e, "event");
+        if ((e = te::launch_batched(P.var, ai, std::min(I.n_items, P.grid), P.threads, P.smem, stream)) !=
+            cudaSuccess)
+            return h->cuda_fail(e, "per-instance launch");
+        ++launches;
+    }
+    if (h->profiling && (e = cudaEventRecord(h->ev1, stream)) != cudaSuccess) return h->cuda_fail(e, "event");
+    if ((e = te::launch_finalize_te(h->d_insts.p, n_inst, h->d_partial.p, h->d_partial_abs.p, digamma_int(k),
+                                    P.err_coef, te_dst, err, stream)) != cudaSuccess)
+        return h->cuda_fail(e, "finalize");
+    ++launches;
+    if (n_groups > 0) {
+        if ((e = te::launch_finalize_groups(h->d_te_all.p, n_groups, S, te_orig, te_surr, p, stream)) !=
+            cudaSuccess)
+            return h->cuda_fail(e, "finalize groups");
+        ++launches;
+    }
+    h->last_launches = launches;
+    h->ev_recorded = h->profiling;
+    return TE_OK;
+}
+
+// upload the plan's tables and run (or replay) the captured graph
+te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int n_series,
+                      const te_instance* inst, int n_inst, int k, double* te_out, double* err,
+                      int32_t* counts, float* eps, int n_groups, int S, double* te_orig,
+                      double* te_surr, double* p, cudaStream_t stream) {
+    te_status st = ensure_psi(h);
+    if (st != TE_OK) return st;
+    bool grew = false;
+    cudaError_t e;
+    if ((e = h->d_insts.ensure(P.insts.size(), &grew)) != cudaSuccess ||
+        (e = h->d_items.ensure(P.items.size(), &grew)) != cudaSuccess ||
+        (e = h->d_words.ensure(2 + (size_t)n_inst, &grew)) != cudaSuccess ||
+        (e = h->d_partial.ensure(P.items.size(), &grew)) != cudaSuccess ||
+        (e = h->d_partial_abs.ensure(P.items.size(), &grew)) != cudaSuccess ||
+        (n_groups > 0 && (e = h->d_te_all.ensure((size_t)n_inst, &grew)) != cudaSuccess))
+        return h->fail(TE_ENOMEM, "workspace: %s", cudaGetErrorString(e));
+    if (grew) {
+        ++h->workspace_gen;
+        // a fresh flag word must start cleared
+        if ((e = cudaMemsetAsync(h->d_words.p, 0, 2 * sizeof(int32_t), stream)) != cudaSuccess)
+            return h->cuda_fail(e, "clear flags");
+    }
+    double* te_dst = n_groups > 0 ? h->d_te_all.p : te_out;
+
+    // signature of everything the captured graph bakes in
+    uint64_t key = 1469598103934665603ull;
+    key = fnv(key, P.insts.data(), P.insts.size() * sizeof(InstDesc));
+    key = fnv(key, P.items.data(), P.items.size() * sizeof(WorkItem));
+    const void* outs[] = {te_out, err, counts, eps, te_orig, te_surr, p};
+    key = fnv(key, outs, sizeof outs);
+    const int cfg[] = {k, P.threads, P.grid, P.smem_floats, P.var.dlo, P.var.dhi, P.var.ks, P.var.qpt,
+                       n_groups, S, h->profiling ? 1 : 0, n_inst};
+    key = fnv(key, cfg, sizeof cfg);
+    const bool replay = !h->per_instance && h->graph_exec && h->graph_key == key &&
+                        h->graph_gen == h->workspace_gen;
+    if (h->per_instance) return run_per_instance(h, P, n_inst, k, te_dst, err, counts, eps, n_groups, S,
+                                                 te_orig, te_surr, p, stream);
+
+    if (!replay) {
+        h->drop_graph();
+        te_status ust = upload_tables(h, P, stream);
+        if (ust != TE_OK) return ust;
+        const BatchArgs a = batch_args(h, P, k, counts, eps);
+        const double psi_k = digamma_int(k);
+
+        cudaGraph_t g = nullptr;
+        if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return h->cuda_fail(e, "begin capture");
+        cudaError_t ce = cudaMemsetAsync(h->d_words.p, 0, sizeof(int32_t), h->cap_stream);
+        int launches = 0;
+        // an event recorded during capture becomes a graph node only with cudaEventRecordExternal
+        if (ce == cudaSuccess && h->profiling) ce = cudaEventRecordWithFlags(h->ev0, h->cap_stream, cudaEventRecordExternal);
+        if (ce == cudaSuccess) {
+            ce = te::launch_batched(P.var, a, P.grid, P.threads, P.smem, h->cap_stream);
+            ++launches;
+        }
+        if (ce == cudaSuccess && h->profiling) ce = cudaEventRecordWithFlags(h->ev1, h->cap_stream, cudaEventRecordExternal);
+        if (ce == cudaSuccess) {
+            ce = te::launch_finalize_te(h->d_insts.p, n_inst, h->d_partial.p, h->d_partial_abs.p, psi_k,
+                                        P.err_coef, te_dst, err, h->cap_stream);
+            ++launches;
+        }
+        if (ce == cudaSuccess && n_groups > 0) {
+            ce = te::launch_finalize_groups(h->d_te_all.p, n_groups, S, te_orig, te_surr, p, h->cap_stream);
+            ++launches;
+        }
+        e = cudaStreamEndCapture(h->cap_stream, &g);
+        if (ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return h->cuda_fail(ce, "kernel launch (capture)");
+        }
+        if (e != cudaSuccess) return h->cuda_fail(e, "end capture");
+        e = cudaGraphInstantiate(&h->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            h->graph_exec = nullptr;
+            return h->cuda_fail(e, "graph instantiate");
+        }
+        h->graph_key = key;
+        h->graph_gen = h->workspace_gen;
+        h->graph_launches = launches;
+    }
+    if ((e = cudaGraphLaunch(h->graph_exec, stream)) != cudaSuccess) return h->cuda_fail(e, "graph launch");
+    h->last_launches = h->graph_launches;
+    h->ev_recorded = h->profiling;
+    (void)series;
+    (void)n_series;
+    (void)inst;
+    return TE_OK;
+}
+
+}  // namespace
+
+// =========================================================================================
+// exported C ABI
+// =========================================================================================
+
+TE_EXPORT te_status te_create(te_handle** out, int32_t device) {
+    if (!out) {
+        g_create_error = "te_create: out is NULL";
+        return TE_EINVAL;
+    }
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("cudaGetDeviceCount: ") + cudaGetErrorString(e);
+        return TE_ECUDA;
+    }
+    if (device < 0 || device >= n) {
+        g_create_error = "te_create: device index out of range";
+        return TE_EINVAL;
+    }
+    DeviceGuard g(device);
+    if (!g.ok) {
+        g_create_error = "te_create: cudaSetDevice failed";
+        return TE_ECUDA;
+    }
+    te_handle* h = new te_handle();
+    h->device = device;
+    cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->upload_done, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreate(&h->ev0)) != cudaSuccess || (e = cudaEventCreate(&h->ev1)) != cudaSuccess) {
+        g_create_error = std::string("te_create: ") + cudaGetErrorString(e);
+        delete h;
+        return TE_ECUDA;
+    }
+    *out = h;
+    return TE_OK;
+}
+
+TE_EXPORT void te_destroy(te_handle* h) {
+    if (!h) return;
+    DeviceGuard g(h->device);
+    cudaStreamSynchronize(h->cap_stream);
+    if (h->upload_done) cudaEventSynchronize(h->upload_done);
+    h->drop_graph();
+    h->d_insts.release();
+    h->d_items.release();
+    h->d_words.release();
+    h->d_partial.release();
+    h->d_partial_abs.release();
+    h->d_te_all.release();
+    h->d_psi.release();
+    h->h_stage.release();
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->upload_done) cudaEventDestroy(h->upload_done);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    delete h;
+}
+
+TE_EXPORT const char* te_last_error(const te_handle* h) {
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+TE_EXPORT te_status te_sync_status(te_handle* h, void* stream) {
+    if (!h) return TE_EINVAL;
+    h->err.clear();
+    DeviceGuard g(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return h->cuda_fail(e, "stream synchronize");
+    if (!h->d_words.p) return TE_OK;
+    int32_t w[2] = {0, 0};
+    if ((e = cudaMemcpyAsync(w, h->d_words.p, sizeof w, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return h->cuda_fail(e, "read flags");
+    if (w[1]) {
+        cudaMemsetAsync(h->d_words.p + 1, 0, sizeof(int32_t), st);
+        cudaStreamSynchronize(st);
+        if (w[1] & te::kFlagBadPerm)
+            return h->fail(TE_EINVAL, "a permutation entry was outside 0..R-1 (clamped to 0)");
+    }
+    return TE_OK;
+}
+
+TE_EXPORT te_status te_embed(te_handle* h, const float* src, const float* tgt, int32_t R, int32_t T,
+                             const te_params* p, const int32_t* src_perm, float* points, int32_t ld,
+                             void* stream) {
+    if (!h) return TE_EINVAL;
+    h->err.clear();
+    if (!src || !tgt || !p || !points) return h->fail(TE_EINVAL, "te_embed: null pointer");
+    if (R < 1 || T < 1) return h->fail(TE_EINVAL, "te_embed: R=%d T=%d", R, T);
+    if (p->d < 1 || p->d > kMaxEmbedDim) return h->fail(TE_EINVAL, "te_embed: d=%d outside 1..%d", p->d, kMaxEmbedDim);
+    if (p->tau < 1 || p->u < 0 || p->window < 1)
+        return h->fail(TE_EINVAL, "te_embed: tau=%d u=%d window=%d", p->tau, p->u, p->window);
+    const int64_t N = (int64_t)R * p->window;
+    if (N > INT32_MAX / 2) return h->fail(TE_EINVAL, "te_embed: N too large");
+    if (ld < N || (ld & 3) || !aligned16(points))
+        return h->fail(TE_EINVAL, "te_embed: ld=%d must be >= N=%lld, a multiple of 4, points 16-byte aligned", ld,
+                       (long long)N);
+    if (!embed_in_range(T, p->d, p->tau, p->u, p->t_start, p->window))
+        return h->fail(TE_ERANGE, "te_embed: t_start=%d window=%d reaches outside 0..%d", p->t_start, p->window, T - 1);
+    DeviceGuard g(h->device);
+    bool grew = false;
+    cudaError_t e = h->d_words.ensure(2, &grew);
+    if (e != cudaSuccess) return h->fail(TE_ENOMEM, "flags: %s", cudaGetErrorString(e));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (grew) {
+        ++h->workspace_gen;
+        cudaMemsetAsync(h->d_words.p, 0, 2 * sizeof(int32_t), st);
+    }
+    e = te::launch_embed(src, tgt, R, T, p->d, p->tau, p->u, p->t_start, p->window, src_perm, points, ld,
+                         h->d_words.p + 1, st);
+    h->last_launches = 1;
+    return e == cudaSuccess ? TE_OK : h->cuda_fail(e, "te_embed launch");
+}
+
+TE_EXPORT te_status te_knn_maxnorm(te_handle* h, const float* points, int32_t N, int32_t D, int32_t ld,
+                                   int32_t k, float* eps, int32_t* nn, void* stream) {
+    if (!h) return TE_EINVAL;
+    h->err.clear();
+    if (!points || !eps) return h->fail(TE_EINVAL, "te_knn_maxnorm: null pointer");
+    if (D < 1 || D > kMaxD) return h->fail(TE_EINVAL, "te_knn_maxnorm: D=%d outside 1..%d", D, kMaxD);
+    if (k < 1 || k > kMaxK) return h->fail(TE_EINVAL, "te_knn_maxnorm: k=%d outside 1..%d", k, kMaxK);
+    if (N < k + 1) return h->fail(TE_EINVAL, "te_knn_maxnorm: N=%d < k+1", N);
+    if (ld < N || (ld & 3) || !aligned16(points))
+        return h->fail(TE_EINVAL, "te_knn_maxnorm: ld=%d must be >= N, a multiple of 4, points 16-byte aligned", ld);
+    DeviceGuard g(h->device);
+    cudaError_t e = te::launch_knn(points, N, D, ld, k, eps, nn, h->sm_count, static_cast<cudaStream_t>(stream));
+    h->last_launches = 1;
+    return e == cudaSuccess ? TE_OK : h->cuda_fail(e, "te_knn_maxnorm launch");
+}
+
+TE_EXPORT te_status te_range_count(te_handle* h, const float* points, int32_t N, int32_t d_y, int32_t d_x,
+                                   int32_t ld, const float* eps, int32_t* counts, void* stream) {
+    if (!h) return TE_EINVAL;
+    h->err.clear();
+    if (!points || !eps || !counts) return h->fail(TE_EINVAL, "te_range_count: null pointer");
+    if (d_y < 0 || d_x < 0 || 1 + d_y + d_x > kMaxD)
+        return h->fail(TE_EINVAL, "te_range_count: d_y=%d d_x=%d", d_y, d_x);
+    if (N < 1) return h->fail(TE_EINVAL, "te_range_count: N=%d", N);
+    if (ld < N || (ld & 3) || !aligned16(points))
+        return h->fail(TE_EINVAL, "te_range_count: ld=%d must be >= N, a multiple of 4, points 16-byte aligned", ld);
+    DeviceGuard g(h->device);
+    cudaError_t e = te::launch_count(points, N, d_y, d_x, ld, eps, counts, h->sm_count,
+                                     static_cast<cudaStream_t>(stream));
+    h->last_launches = 1;
+    return e == cudaSuccess ? TE_OK : h->cuda_fail(e, "te_range_count launch");
+}
+
+TE_EXPORT te_status te_estimate(te_handle* h, const te_series* series, int32_t n_series,
+                                const te_instance* inst, int32_t n_inst, int32_t k, double* te,
+                                double* err_bound, int32_t* counts, float* eps, void* stream) {
+    if (!h) return TE_EINVAL;
+    h->err.clear();
+    if (k < 1 || k > kMaxK) return h->fail(TE_EINVAL, "te_estimate: k=%d outside 1..%d", k, kMaxK);
+    if (n_inst < 0 || (n_inst > 0 && (!inst || !te))) return h->fail(TE_EINVAL, "te_estimate: null instances/te");
+    te_status st = validate_series(h, series, n_series);
+    if (st != TE_OK) return st;
+    if (n_inst == 0) {
+        h->last_launches = 0;
+        return TE_OK;
+    }
+    DeviceGuard g(h->device);
+    Plan P;
+    if ((st = build_plan(h, series, n_series, inst, n_inst, k, &P)) != TE_OK) return st;
+    return run_batched(h, P, series, n_series, inst, n_inst, k, te, err_bound, counts, eps, 0, 0, nullptr,
+                       nullptr, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+TE_EXPORT te_status te_surrogate_test(te_handle* h, const te_series* series, int32_t n_series,
+                                      const int32_t* t_starts, int32_t n_t, int32_t window, int32_t S,
+                                      int32_t k, double* te_orig, double* te_surr, double* p, void* stream) {
+    if (!h) return TE_EINVAL;
+    h->err.clear();
+    if (k < 1 || k > kMaxK) return h->fail(TE_EINVAL, "te_surrogate_test: k=%d outside 1..%d", k, kMaxK);
+    if (n_t < 0 || S < 0 || window < 1 || (n_t > 0 && !t_starts))
+        return h->fail(TE_EINVAL, "te_surrogate_test: n_t=%d S=%d window=%d", n_t, S, window);
+    if (!te_orig || !p || (S > 0 && !te_surr)) return h->fail(TE_EINVAL, "te_surrogate_test: null output");
+    te_status st = validate_series(h, series, n_series);
+    if (st != TE_OK) return st;
+    for (int s = 0; s < n_series; ++s)
+        if (series[s].S < S) return h->fail(TE_EINVAL, "series %d has %d permutations < S=%d", s, series[s].S, S);
+    const int64_t n_inst64 = (int64_t)n_series * n_t * (S + 1);
+    if (n_inst64 > INT32_MAX / 4) return h->fail(TE_ENOTIMPL, "te_surrogate_test: too many estimates");
+    if (n_inst64 == 0) {
+        h->last_launches = 0;
+        return TE_OK;
+    }
+    std::vector<te_instance> inst;
+    inst.reserve((size_t)n_inst64);
+    for (int s = 0; s < n_series; ++s)
+        for (int j = 0; j < n_t; ++j)
+            for (int m = -1; m < S; ++m) inst.push_back(te_instance{s, t_starts[j], window, m});
+    DeviceGuard g(h->device);
+    Plan P;
+    if ((st = build_plan(h, series, n_series, inst.data(), (int)inst.size(), k, &P)) != TE_OK) return st;
+    return run_batched(h, P, series, n_series, inst.data(), (int)inst.size(), k, nullptr, nullptr, nullptr,
+                       nullptr, n_series * n_t, S, te_orig, te_surr, p, static_cast<cudaStream_t>(stream));
+}
+
+TE_EXPORT te_status te_set_profiling(te_handle* h, int32_t enable) {
+    if (!h) return TE_EINVAL;
+    h->profiling = enable != 0;
+    return TE_OK;
+}
+
+TE_EXPORT te_status te_last_kernel_ms(te_handle* h, float* ms) {
+    if (!h || !ms) return TE_EINVAL;
+    h->err.clear();
+    if (!h->ev_recorded) return h->fail(TE_EINVAL, "no profiled batched launch yet");
+    DeviceGuard g(h->device);
+    cudaError_t e = cudaEventSynchronize(h->ev1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, h->ev0, h->ev1);
+    return e == cudaSuccess ? TE_OK : h->cuda_fail(e, "kernel timing");
+}
+
+TE_EXPORT int32_t te_last_launch_count(const te_handle* h) { return h ? h->last_launches : 0; }
+
+TE_EXPORT te_status te_set_batching(te_handle* h, int32_t per_instance) {
+    if (!h) return TE_EINVAL;
+    h->per_instance = per_instance != 0;
+    return TE_OK;
+}
+
+TE_EXPORT te_status te_set_launch_config(te_handle* h, int32_t threads, int32_t qpt) {
+    if (!h) return TE_EINVAL;
+    h->err.clear();
+    if (threads != 0 && (threads < 64 || threads > te::kBatchedMaxThreads || threads % 32))
+        return h->fail(TE_EINVAL, "threads=%d: multiple of 32 in 64..%d or 0", threads, te::kBatchedMaxThreads);
+    if (qpt != 0 && qpt != 2 && qpt != 4) return h->fail(TE_EINVAL, "qpt=%d: 2, 4 or 0", qpt);
+    h->cfg_threads = threads;
+    h->cfg_qpt = qpt;
+    return TE_OK;
+}

@@ -1,0 +1,74 @@
+// Internal declarations shared by the library's translation units (host + device).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "te_gb300.h"
+
+namespace te {
+
+// Device-side descriptor of one estimate: where its points come from (Eq. 6/7/10) and where
+// its work items and per-point outputs live.
+struct InstDesc {
+    const float* src;      // source series [R][T]
+    const float* tgt;      // target series [R][T]
+    const int32_t* perm;   // source repetition paired with target repetition r, or nullptr
+    int32_t R, T, W, t_start;
+    int32_t tau, u, d, N;  // N = R * W points, joint dimension 1 + 2d
+    int64_t pt_off;        // offset of this instance's points in concatenated eps/counts outputs
+    int32_t item_begin;    // its work items are item_begin .. item_begin + n_items - 1
+    int32_t n_items;
+};
+
+// One unit of work of the persistent kernel: queries q0 .. q0 + threads*qpt - 1 of an instance.
+struct WorkItem {
+    int32_t inst;
+    int32_t q0;
+};
+
+// Largest CTA of the persistent batched kernel (its __launch_bounds__).
+constexpr int kBatchedMaxThreads = 512;
+
+// Bits of the device flag word.
+enum : int32_t { kFlagBadPerm = 1 };
+
+struct BatchArgs {
+    const InstDesc* insts;
+    const WorkItem* items;
+    int32_t n_items;
+    int32_t* queue;          // work-queue head, zeroed before every launch
+    int32_t* flags;          // device flag word (kFlag*)
+    const float2* psi;       // psi(n) as (hi, lo) float pair, n = 0 .. psi_n-1 (entry 0 unused)
+    int32_t k;
+    int32_t smem_floats;     // floats of dynamic shared memory (reference tile capacity * D)
+    double* partial;         // [n_items] per-item sum of the Eq. 9 digamma terms
+    double* partial_abs;     // [n_items] per-item sum of |terms| (for the error bound)
+    int32_t* counts_out;     // nullable: per instance [3][N] at 3 * pt_off
+    float* eps_out;          // nullable: per instance [N] at pt_off
+};
+
+// ---- launchers (te_unit.cu) ----
+cudaError_t launch_embed(const float* src, const float* tgt, int R, int T, int d, int tau, int u,
+                         int t_start, int W, const int32_t* perm, float* points, int ld,
+                         int32_t* flags, cudaStream_t s);
+cudaError_t launch_knn(const float* pts, int N, int D, int ld, int k, float* eps, int32_t* nn,
+                       int sm_count, cudaStream_t s);
+cudaError_t launch_count(const float* pts, int N, int dy, int dx, int ld, const float* eps,
+                         int32_t* counts, int sm_count, cudaStream_t s);
+
+// ---- launchers (te_batched_*.cu, te_finalize.cu) ----
+// Variant of the persistent kernel: d in [dlo, dhi] (dlo == dhi: specialised), ks = k-slots.
+struct BatchedVariant {
+    int dlo, dhi, ks, qpt;
+};
+const void* batched_kernel_ptr(const BatchedVariant& v);
+cudaError_t launch_batched(const BatchedVariant& v, const BatchArgs& a, int grid, int threads,
+                           size_t smem, cudaStream_t s);
+cudaError_t launch_finalize_te(const InstDesc* insts, int n_inst, const double* partial,
+                               const double* partial_abs, double psi_k, double err_coef,
+                               double* te, double* err, cudaStream_t s);
+cudaError_t launch_finalize_groups(const double* te_all, int n_groups, int S, double* te_orig,
+                                   double* te_surr, double* p, cudaStream_t s);
+
+}  // namespace te

@@ -1,0 +1,311 @@
+"""Python binding of the C ABI in ``include/te_gb300.h`` (ctypes; argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no arithmetic of the
+method: it checks tensor devices/dtypes/layouts, allocates outputs with torch when the caller
+passes none, converts descriptors to the C structs and raises ``TEError`` on a non-zero
+status. PyTorch supplies device memory and the current CUDA stream.
+
+The shared library is the in-tree ``_lib/libte_gb300.so`` built by ``build.build()``; there is
+no other implementation to fall back to, so a missing library raises immediately.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+TE_OK, TE_EINVAL, TE_ERANGE, TE_ENOMEM, TE_ECUDA, TE_ETIMEOUT, TE_ENOTIMPL = range(7)
+_STATUS = {0: "TE_OK", 1: "TE_EINVAL", 2: "TE_ERANGE", 3: "TE_ENOMEM", 4: "TE_ECUDA",
+           5: "TE_ETIMEOUT", 6: "TE_ENOTIMPL"}
+
+# every symbol the header declares (checked by the tests against include/te_gb300.h)
+EXPORTS = ["te_create", "te_destroy", "te_last_error", "te_sync_status", "te_embed",
+           "te_knn_maxnorm", "te_range_count", "te_estimate", "te_surrogate_test",
+           "te_set_profiling", "te_last_kernel_ms", "te_last_launch_count", "te_set_launch_config",
+           "te_set_batching"]
+
+
+class TEError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class te_params(C.Structure):
+    _fields_ = [("d", C.c_int32), ("tau", C.c_int32), ("u", C.c_int32), ("k", C.c_int32),
+                ("t_start", C.c_int32), ("window", C.c_int32)]
+
+
+class te_series(C.Structure):
+    _fields_ = [("src", C.c_void_p), ("tgt", C.c_void_p), ("R", C.c_int32), ("T", C.c_int32),
+                ("d", C.c_int32), ("tau", C.c_int32), ("u", C.c_int32), ("S", C.c_int32),
+                ("perms", C.c_void_p)]
+
+
+class te_instance(C.Structure):
+    _fields_ = [("series", C.c_int32), ("t_start", C.c_int32), ("window", C.c_int32),
+                ("perm", C.c_int32)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load() -> C.CDLL:
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built ({path} missing): run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    P, i32 = C.c_void_p, C.c_int32
+    lib.te_create.argtypes = [C.POINTER(P), i32]
+    lib.te_create.restype = i32
+    lib.te_destroy.argtypes = [P]
+    lib.te_destroy.restype = None
+    lib.te_last_error.argtypes = [P]
+    lib.te_last_error.restype = C.c_char_p
+    lib.te_sync_status.argtypes = [P, P]
+    lib.te_embed.argtypes = [P, P, P, i32, i32, C.POINTER(te_params), P, P, i32, P]
+    lib.te_knn_maxnorm.argtypes = [P, P, i32, i32, i32, i32, P, P, P]
+    lib.te_range_count.argtypes = [P, P, i32, i32, i32, i32, P, P, P]
+    lib.te_estimate.argtypes = [P, C.POINTER(te_series), i32, C.POINTER(te_instance), i32, i32,
+                                P, P, P, P, P]
+    lib.te_surrogate_test.argtypes = [P, C.POINTER(te_series), i32, P, i32, i32, i32, i32, P, P,
+                                      P, P]
+    lib.te_set_profiling.argtypes = [P, i32]
+    lib.te_last_kernel_ms.argtypes = [P, C.POINTER(C.c_float)]
+    lib.te_last_launch_count.argtypes = [P]
+    lib.te_set_launch_config.argtypes = [P, i32, i32]
+    lib.te_set_batching.argtypes = [P, i32]
+    for name in ("te_sync_status", "te_embed", "te_knn_maxnorm", "te_range_count", "te_estimate",
+                 "te_surrogate_test", "te_set_profiling", "te_last_kernel_ms",
+                 "te_last_launch_count", "te_set_launch_config", "te_set_batching"):
+        getattr(lib, name).restype = i32
+    _lib = lib
+    return lib
+
+
+# ------------------------------------------------------------------------------- helpers
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _need(t: torch.Tensor, dtype, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Handle:
+    """Owner of a ``te_handle*`` (device workspace, cached plans and graphs)."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        h = C.c_void_p()
+        st = self.lib.te_create(C.byref(h), int(device))
+        if st != TE_OK:
+            raise TEError(st, self.lib.te_last_error(None).decode())
+        self.h = h
+        self.device = int(device)
+
+    def check(self, st: int):
+        if st != TE_OK:
+            raise TEError(st, self.lib.te_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.te_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def te_create(device: int = 0) -> Handle:
+    return Handle(device)
+
+
+def te_destroy(h: Handle):
+    h.close()
+
+
+def te_last_error(h: Optional[Handle]) -> str:
+    lib = load()
+    return lib.te_last_error(None if h is None else h.h).decode()
+
+
+def te_sync_status(h: Handle, stream=None):
+    h.check(h.lib.te_sync_status(h.h, _stream(stream)))
+
+
+def te_embed(h: Handle, src: torch.Tensor, tgt: torch.Tensor, d: int, tau: int, u: int,
+             t_start: int, window: int, perm: Optional[torch.Tensor] = None,
+             points: Optional[torch.Tensor] = None, ld: Optional[int] = None, stream=None):
+    """Points [D][ld] (SoA) of one estimate; returns (points, N, D, ld)."""
+    _need(src, torch.float32, "src")
+    _need(tgt, torch.float32, "tgt")
+    R, T = src.shape
+    N = R * window
+    D = 1 + 2 * d
+    ld = ld or ((N + 3) // 4) * 4
+    if points is None:
+        points = torch.empty((D, ld), dtype=torch.float32, device=src.device)
+    _need(points, torch.float32, "points")
+    if perm is not None:
+        _need(perm, torch.int32, "perm")
+    p = te_params(d, tau, u, 0, t_start, window)
+    h.check(h.lib.te_embed(h.h, _ptr(src), _ptr(tgt), R, T, C.byref(p), _ptr(perm), _ptr(points),
+                           ld, _stream(stream)))
+    return points, N, D, ld
+
+
+def te_knn_maxnorm(h: Handle, points: torch.Tensor, N: int, D: int, ld: int, k: int,
+                   eps: Optional[torch.Tensor] = None, want_nn: bool = False, stream=None):
+    _need(points, torch.float32, "points")
+    if eps is None:
+        eps = torch.empty(N, dtype=torch.float32, device=points.device)
+    nn = torch.empty((N, k), dtype=torch.int32, device=points.device) if want_nn else None
+    h.check(h.lib.te_knn_maxnorm(h.h, _ptr(points), N, D, ld, k, _ptr(eps), _ptr(nn),
+                                 _stream(stream)))
+    return (eps, nn) if want_nn else eps
+
+
+def te_range_count(h: Handle, points: torch.Tensor, N: int, d_y: int, d_x: int, ld: int,
+                   eps: torch.Tensor, counts: Optional[torch.Tensor] = None, stream=None):
+    _need(points, torch.float32, "points")
+    _need(eps, torch.float32, "eps")
+    if counts is None:
+        counts = torch.empty((3, N), dtype=torch.int32, device=points.device)
+    h.check(h.lib.te_range_count(h.h, _ptr(points), N, d_y, d_x, ld, _ptr(eps), _ptr(counts),
+                                 _stream(stream)))
+    return counts
+
+
+@dataclass
+class DeviceSeries:
+    """Device copies of one series (and its permutations) plus the C descriptor."""
+    src: torch.Tensor
+    tgt: torch.Tensor
+    d: int
+    tau: int
+    u: int
+    perms: Optional[torch.Tensor] = None
+
+    @property
+    def S(self) -> int:
+        return 0 if self.perms is None else int(self.perms.shape[0])
+
+    def desc(self) -> te_series:
+        return te_series(self.src.data_ptr(), self.tgt.data_ptr(), self.src.shape[0],
+                         self.src.shape[1], self.d, self.tau, self.u, self.S,
+                         None if self.perms is None else self.perms.data_ptr())
+
+
+def to_device(series: Sequence, device="cuda", non_blocking: bool = False) -> List[DeviceSeries]:
+    """Copy host series (objects with src, tgt, d, tau, u, perms as numpy or torch) to the GPU."""
+    out = []
+    for s in series:
+        def dev(a, dt):
+            if a is None:
+                return None
+            t = a if isinstance(a, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(a))
+            return t.to(device=device, dtype=dt, non_blocking=non_blocking).contiguous()
+        out.append(DeviceSeries(dev(s.src, torch.float32), dev(s.tgt, torch.float32), int(s.d),
+                                int(s.tau), int(s.u), dev(s.perms, torch.int32)))
+    return out
+
+
+def _series_array(series: Sequence[DeviceSeries]):
+    arr = (te_series * len(series))()
+    for i, s in enumerate(series):
+        arr[i] = s.desc()
+    return arr
+
+
+def te_estimate(h: Handle, series: Sequence[DeviceSeries], instances: Sequence, k: int,
+                te: Optional[torch.Tensor] = None, want_err: bool = False,
+                want_counts: bool = False, stream=None):
+    """TE of every instance (objects with series, t_start, window, perm) in one batched launch.
+    Returns te [n] (float64) or a dict with te, err_bound, counts, eps when asked."""
+    dev = series[0].src.device
+    n = len(instances)
+    ser = _series_array(series)
+    ins = (te_instance * max(1, n))()
+    npts = 0
+    for i, it in enumerate(instances):
+        ins[i] = te_instance(int(it.series), int(it.t_start), int(it.window), int(it.perm))
+        if 0 <= int(it.series) < len(series):  # the library validates the rest
+            npts += series[int(it.series)].src.shape[0] * int(it.window)
+    if te is None:
+        te = torch.empty(n, dtype=torch.float64, device=dev)
+    err = torch.empty(n, dtype=torch.float64, device=dev) if want_err else None
+    counts = torch.empty(3 * npts, dtype=torch.int32, device=dev) if want_counts else None
+    eps = torch.empty(npts, dtype=torch.float32, device=dev) if want_counts else None
+    h.check(h.lib.te_estimate(h.h, ser, len(series), ins, n, int(k), _ptr(te), _ptr(err),
+                              _ptr(counts), _ptr(eps), _stream(stream)))
+    if not (want_err or want_counts):
+        return te
+    return {"te": te, "err_bound": err, "counts": counts, "eps": eps}
+
+
+def te_surrogate_test(h: Handle, series: Sequence[DeviceSeries], t_starts: Sequence[int],
+                      window: int, S: int, k: int, out=None, stream=None):
+    """Original TE, S surrogate TEs and the p-value per (series, t_start)."""
+    dev = series[0].src.device
+    ns, nt = len(series), len(t_starts)
+    ser = _series_array(series)
+    ts = (C.c_int32 * max(1, nt))(*[int(t) for t in t_starts])
+    if out is None:
+        out = {"te_orig": torch.empty((ns, nt), dtype=torch.float64, device=dev),
+               "te_surr": torch.empty((ns, nt, max(S, 1)), dtype=torch.float64, device=dev),
+               "p": torch.empty((ns, nt), dtype=torch.float64, device=dev)}
+    h.check(h.lib.te_surrogate_test(h.h, ser, ns, C.cast(ts, C.c_void_p), nt, int(window),
+                                    int(S), int(k), _ptr(out["te_orig"]), _ptr(out["te_surr"]),
+                                    _ptr(out["p"]), _stream(stream)))
+    return out
+
+
+def te_set_profiling(h: Handle, enable: bool):
+    h.check(h.lib.te_set_profiling(h.h, 1 if enable else 0))
+
+
+def te_last_kernel_ms(h: Handle) -> float:
+    ms = C.c_float()
+    h.check(h.lib.te_last_kernel_ms(h.h, C.byref(ms)))
+    return float(ms.value)
+
+
+def te_last_launch_count(h: Handle) -> int:
+    return int(h.lib.te_last_launch_count(h.h))
+
+
+def te_set_launch_config(h: Handle, threads: int = 0, qpt: int = 0):
+    h.check(h.lib.te_set_launch_config(h.h, int(threads), int(qpt)))
+
+
+def te_set_batching(h: Handle, per_instance: bool):
+    h.check(h.lib.te_set_batching(h.h, 1 if per_instance else 0))

@@ -14,3 +14,16 @@ if HERE not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+@pytest.fixture(scope="session")
+def te_handle():
+    """A library handle on cuda:0 (builds the library if it is missing)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_1401_4068_gb300 import build, te
+    build.build()
+    h = te.Handle(0)
+    yield h
+    h.close()
