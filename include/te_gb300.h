@@ -179,6 +179,29 @@ te_status te_set_launch_config(te_handle* h, int32_t threads, int32_t qpt);
  * Implementation section's "several chunks per launch" design). Results are bit-identical. */
 te_status te_set_batching(te_handle* h, int32_t per_instance);
 
+/* te_surrogate_test_static - te_surrogate_test for one series, for callers that cannot allocate
+ * GPU memory. The paper has no counterpart: this exists for embedding the library where
+ * cudaMalloc is not allowed (a host process whose device memory is owned by another runtime or
+ * pool, a fixed memory budget, code that must not cause the implicit synchronisation an
+ * allocation can bring). It needs no handle and allocates nothing on the device or the host.
+ * Its scratch (work-queue head, per-item partial sums, per-estimate TE, digamma table) is one
+ * fixed static device array of about 2.6 MiB that every GPU loading the library holds until
+ * the process exits.
+ *   Runs on the calling thread's current device. The first call on a device sets it up (looks
+ *   up the array's device address, fills the digamma table, sets kernel attributes): make that
+ *   call before any stream capture. Calls reuse the array; the queue head is cleared on each
+ *   call and every other value is rewritten before it is read. Calls whose GPU work overlaps
+ *   (other streams or host threads) race on the array and must be serialised by the caller.
+ *   Limits: k <= 4, d = 1..5, N = R * window <= 8192, n_t <= 256, n_t * (S + 1) <= 65536
+ *   estimates; beyond them TE_ENOTIMPL and a message. Out-of-range permutation entries are
+ *   read as repetition 0 (no flag is reported).
+ *   Outputs as te_surrogate_test with n_series = 1: te_orig [n_t], te_surr [n_t][S], p [n_t].
+ *   msg (nullable, msg_len bytes) receives the reason of a failed call. */
+te_status te_surrogate_test_static(const te_series* series, const int32_t* t_starts, int32_t n_t,
+                                   int32_t window, int32_t S, int32_t k, double* te_orig,
+                                   double* te_surr, double* p, void* stream, char* msg,
+                                   int32_t msg_len);
+
 #ifdef __cplusplus
 }
 #endif

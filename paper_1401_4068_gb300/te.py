@@ -28,7 +28,7 @@ _STATUS = {0: "TE_OK", 1: "TE_EINVAL", 2: "TE_ERANGE", 3: "TE_ENOMEM", 4: "TE_EC
 EXPORTS = ["te_create", "te_destroy", "te_last_error", "te_sync_status", "te_embed",
            "te_knn_maxnorm", "te_range_count", "te_estimate", "te_surrogate_test",
            "te_set_profiling", "te_last_kernel_ms", "te_last_launch_count", "te_set_launch_config",
-           "te_set_batching"]
+           "te_set_batching", "te_surrogate_test_static"]
 
 
 class TEError(RuntimeError):
