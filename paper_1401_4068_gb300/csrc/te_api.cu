@@ -219,10 +219,15 @@ te_status validate_series(te_handle* h, const te_series* series, int n_series) {
     return TE_OK;
 }
 
-// choose CTA size and queries per thread for a batch
+// choose CTA size and queries per thread for a batch: 4 queries per thread (2 when d = 5 or
+// k > 4, where 4 would not fit the register budget), and for a uniform point count the CTA size
+// with the fewest padded query slots, ties to the smallest CTA of at least 128 threads (several
+// CTAs per SM hide the per-item barriers)
 void choose_shape(te_handle* h, const std::vector<InstDesc>& insts, int ks, int* threads, int* qpt) {
-    int q = h->cfg_qpt ? h->cfg_qpt : (ks == 5 ? 4 : 2);
-    if (ks != 5) q = 2;
+    int dmax = 1;
+    for (const auto& I : insts) dmax = std::max(dmax, I.d);
+    int q = (ks == 5 && dmax <= 4) ? 4 : 2;
+    if (h->cfg_qpt) q = ks == 5 ? h->cfg_qpt : 2;
     *qpt = q;
     if (h->cfg_threads) {
         *threads = h->cfg_threads;
@@ -234,21 +239,18 @@ void choose_shape(te_handle* h, const std::vector<InstDesc>& insts, int ks, int*
         *threads = 256;
         return;
     }
-    // uniform N: fewest padded query slots, then the CTA size nearest 256
     const int N = insts[0].N;
-    int best_t = 256;
+    int best_t = 0;
     int64_t best_slots = INT64_MAX;
-    for (int m = 1; m <= 64; ++m) {
-        int t = 32 * ((N + m * q * 32 - 1) / (m * q * 32));
-        if (t < 64) t = 64;
-        if (t > te::kBatchedMaxThreads) continue;
+    for (int t = 64; t <= te::kBatchedMaxThreads; t += 32) {
         const int64_t per = (int64_t)t * q;
         const int64_t slots = ((N + per - 1) / per) * per;
-        if (slots < best_slots || (slots == best_slots && std::abs(t - 256) < std::abs(best_t - 256))) {
+        const bool better = slots < best_slots ||
+                            (slots == best_slots && best_t < 128 && t >= 128);
+        if (better) {
             best_slots = slots;
             best_t = t;
         }
-        if (t == 64) break;
     }
     *threads = best_t;
 }

@@ -46,17 +46,20 @@ __device__ __forceinline__ void process_item(const BatchArgs& a, const InstDesc&
     const int ldt = (a.smem_floats / D) & ~3;  // references per tile
     const int ntile = (N + ldt - 1) / ldt;
 
-    // queries of this thread: q0 + threadIdx.x + q * T
-    float qc[Q][D];
+    // queries of this thread: q0 + threadIdx.x + q * T, each coordinate duplicated (q, q)
+    u64 qq[Q][D];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int i = q0 + threadIdx.x + q * T;
+        float p[D];
         if (i < N) {
-            gather_point<d>(I, i, qc[q], a.flags);
+            gather_point<d>(I, i, p, a.flags);
         } else {
 #pragma unroll
-            for (int c = 0; c < D; ++c) qc[q][c] = 0.0f;
+            for (int c = 0; c < D; ++c) p[c] = 0.0f;
         }
+#pragma unroll
+        for (int c = 0; c < D; ++c) qq[q][c] = dup2(p[c]);
     }
     // warps whose first query is past N have nothing to compute (warp-uniform)
     const bool warp_active = q0 + (int)(threadIdx.x & ~31u) < N;
@@ -73,16 +76,16 @@ __device__ __forceinline__ void process_item(const BatchArgs& a, const InstDesc&
         __syncthreads();
         stage_tile<d>(I, base, nv, ldt, sm, a.flags);
         __syncthreads();
-        if (warp_active) knn_tile<D, Q, KS>(sm, ldt, (nv + 3) >> 2, qc, t);
+        if (warp_active) knn_tile<D, Q, KS>(sm, ldt, (nv + 3) >> 2, qq, t);
     }
     float e[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) e[q] = topk_select(t[q], a.k);
 
     // ---- pass 2: strict counts in the marginal spaces
-    int cz[Q], cyz[Q], cxz[Q];
+    float cz[Q], cyz[Q], cxz[Q];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) cz[q] = cyz[q] = cxz[q] = 0;
+    for (int q = 0; q < Q; ++q) cz[q] = cyz[q] = cxz[q] = 0.0f;
     for (int tile = 0; tile < ntile; ++tile) {
         const int base = tile * ldt;
         const int nv = min(ldt, N - base);
@@ -91,7 +94,7 @@ __device__ __forceinline__ void process_item(const BatchArgs& a, const InstDesc&
             stage_tile<d>(I, base, nv, ldt, sm, a.flags);
             __syncthreads();
         }
-        if (warp_active) count_tile<d, d, Q>(sm, ldt, (nv + 3) >> 2, qc, e, cz, cyz, cxz);
+        if (warp_active) count_tile<d, d, Q>(sm, ldt, (nv + 3) >> 2, qq, e, cz, cyz, cxz);
     }
 
     // ---- digamma terms of Eq. 9, compensated FP32 per thread
@@ -102,7 +105,7 @@ __device__ __forceinline__ void process_item(const BatchArgs& a, const InstDesc&
         const int i = q0 + threadIdx.x + q * T;
         if (i < N) {
             const int self = e[q] > 0.0f ? 1 : 0;  // the point itself was counted at distance 0
-            const int nz = cz[q] - self, nyz = cyz[q] - self, nxz = cxz[q] - self;
+            const int nz = (int)cz[q] - self, nyz = (int)cyz[q] - self, nxz = (int)cxz[q] - self;
             if (a.counts_out) {
                 int32_t* co = a.counts_out + 3 * I.pt_off;
                 co[i] = nz;

@@ -16,11 +16,6 @@ namespace te {
 
 __device__ __forceinline__ float f_inf() { return __int_as_float(0x7f800000); }
 
-template <int E>
-__device__ __forceinline__ float comp(const float4& v) {
-    return E == 0 ? v.x : (E == 1 ? v.y : (E == 2 ? v.z : v.w));
-}
-
 // ---------------------------------------------------------------------------------------
 // Top-(k+1) of all N distances, self included. The point's distance to itself is 0, the
 // smallest possible value, so the (k+1)-th smallest over all j equals the k-th smallest over
@@ -47,77 +42,134 @@ __device__ __forceinline__ float topk_select(const float (&t)[KS], int k) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Packed FP32 forms of sm_100-family GPUs, written as inline PTX:
+//   sub.rn.f32x2   two IEEE round-to-nearest subtractions in one instruction (each lane of the
+//                  pair is exactly fl32(a - b));
+//   max.abs.f32    with three inputs: max(|a|, |b|, |c|), two new coordinates per instruction;
+//   set.lt.f32.f32 1.0f if a < b else 0.0f.
+// A query coordinate is kept duplicated in a 64-bit register pair (q, q) so that one packed
+// subtraction covers two references.
+// ---------------------------------------------------------------------------------------
+typedef unsigned long long u64;
+
+__device__ __forceinline__ u64 dup2(float q) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(q));
+    return r;
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
+    u64 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ void split2(u64 v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ float absmax3(float a, float b, float c) {
+    float d;
+    asm("max.abs.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float set_lt(float a, float b) {
+    float d;
+    asm("set.lt.f32.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ float abs_set_lt(float a, float b) {
+    float d;
+    asm("{.reg .f32 t; abs.f32 t, %1; set.lt.f32.f32 %0, t, %2;}" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
+// max |v[c]| over c = C0 .. C1 (inclusive, C1 >= C0), three inputs per instruction
+template <int C0, int C1, int N>
+__device__ __forceinline__ float absmax_range(const float (&v)[N]) {
+    constexpr int n = C1 - C0 + 1;
+    float m = absmax3(v[C0], v[n >= 2 ? C0 + 1 : C0], v[n >= 3 ? C0 + 2 : (n >= 2 ? C0 + 1 : C0)]);
+#pragma unroll
+    for (int c = C0 + 3; c <= C1; c += 2) m = absmax3(m, v[c], v[c + 1 <= C1 ? c + 1 : c]);
+    return m;
+}
+
+// the D coordinate differences of one query against four references, unpacked per reference
+template <int D>
+__device__ __forceinline__ void diff4(const u64 (&qq)[D], const ulonglong2 (&r)[D], float (&dx)[D],
+                                      float (&dy)[D], float (&dz)[D], float (&dw)[D]) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        split2(sub2(qq[c], r[c].x), dx[c], dy[c]);
+        split2(sub2(qq[c], r[c].y), dz[c], dw[c]);
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void load_refs4(const float* __restrict__ s, int ldt, int j, ulonglong2 (&r)[D]) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) r[c] = *reinterpret_cast<const ulonglong2*>(s + c * ldt + 4 * j);
+}
+
+// ---------------------------------------------------------------------------------------
 // Pass 1 over one staged reference tile: smem holds coordinate c of reference j at
 // s[c * ldt + j] (structure of arrays, +inf past the last valid reference). Every thread
 // streams the whole tile against its Q register-resident queries; four references are
-// read per float4 broadcast load.
+// read per 128-bit broadcast load.
 // ---------------------------------------------------------------------------------------
 template <int D, int Q, int KS>
 __device__ __forceinline__ void knn_tile(const float* __restrict__ s, int ldt, int n4,
-                                         const float (&qc)[Q][D], float (&t)[Q][KS]) {
+                                         const u64 (&qq)[Q][D], float (&t)[Q][KS]) {
 #pragma unroll 1
     for (int j = 0; j < n4; ++j) {
-        float4 r[D];
-#pragma unroll
-        for (int c = 0; c < D; ++c) r[c] = *reinterpret_cast<const float4*>(s + c * ldt + 4 * j);
+        ulonglong2 r[D];
+        load_refs4<D>(s, ldt, j, r);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            float m0 = fabsf(qc[q][0] - r[0].x);
-            float m1 = fabsf(qc[q][0] - r[0].y);
-            float m2 = fabsf(qc[q][0] - r[0].z);
-            float m3 = fabsf(qc[q][0] - r[0].w);
-#pragma unroll
-            for (int c = 1; c < D; ++c) {
-                m0 = fmaxf(m0, fabsf(qc[q][c] - r[c].x));
-                m1 = fmaxf(m1, fabsf(qc[q][c] - r[c].y));
-                m2 = fmaxf(m2, fabsf(qc[q][c] - r[c].z));
-                m3 = fmaxf(m3, fabsf(qc[q][c] - r[c].w));
-            }
-            topk_push(t[q], m0);
-            topk_push(t[q], m1);
-            topk_push(t[q], m2);
-            topk_push(t[q], m3);
+            float dx[D], dy[D], dz[D], dw[D];
+            diff4<D>(qq[q], r, dx, dy, dz, dw);
+            topk_push(t[q], absmax_range<0, D - 1>(dx));
+            topk_push(t[q], absmax_range<0, D - 1>(dy));
+            topk_push(t[q], absmax_range<0, D - 1>(dz));
+            topk_push(t[q], absmax_range<0, D - 1>(dw));
         }
     }
 }
 
 // ---------------------------------------------------------------------------------------
 // Pass 2 over one staged tile: grouped maxima a = |dy_t|, b = max |dy-|, x = max |dx-| and
-// the three strict counts of Eq. 9: n_z (b < e), n_yz (max(a,b) < e), n_xz (max(b,x) < e).
-// The query itself is included here (a = b = x = 0) and removed by the caller.
+// the three strict counts of Eq. 9: n_z (b < e), n_yz (max(a,b) < e, i.e. a < e and b < e),
+// n_xz (max(b,x) < e, i.e. b < e and x < e). Indicators are 1.0f / 0.0f; the products of two
+// indicators and the sums stay exact in FP32 (counts < 2^24). The query itself is included
+// here (a = b = x = 0) and removed by the caller. Requires DY >= 1 and DX >= 1.
 // ---------------------------------------------------------------------------------------
-template <int DY, int DX, int Q, int E>
-__device__ __forceinline__ void count_one(const float (&q)[1 + DY + DX], const float4 (&r)[1 + DY + DX],
-                                          float e, int& cz, int& cyz, int& cxz) {
-    const float a = fabsf(q[0] - comp<E>(r[0]));
-    float b = 0.0f;
-#pragma unroll
-    for (int c = 1; c <= DY; ++c) b = (c == 1) ? fabsf(q[c] - comp<E>(r[c])) : fmaxf(b, fabsf(q[c] - comp<E>(r[c])));
-    float x = 0.0f;
-#pragma unroll
-    for (int c = DY + 1; c <= DY + DX; ++c)
-        x = (c == DY + 1) ? fabsf(q[c] - comp<E>(r[c])) : fmaxf(x, fabsf(q[c] - comp<E>(r[c])));
-    cz += (b < e) ? 1 : 0;
-    cyz += (fmaxf(a, b) < e) ? 1 : 0;
-    cxz += (fmaxf(b, x) < e) ? 1 : 0;
+template <int DY, int DX>
+__device__ __forceinline__ void count_one(const float (&d)[1 + DY + DX], float e, float& cz, float& cyz,
+                                          float& cxz) {
+    const float b = absmax_range<1, DY>(d);
+    const float x = absmax_range<DY + 1, DY + DX>(d);
+    const float sb = set_lt(b, e);
+    const float sa = abs_set_lt(d[0], e);
+    const float sx = set_lt(x, e);
+    cz += sb;
+    cyz = fmaf(sa, sb, cyz);
+    cxz = fmaf(sx, sb, cxz);
 }
 
 template <int DY, int DX, int Q>
 __device__ __forceinline__ void count_tile(const float* __restrict__ s, int ldt, int n4,
-                                           const float (&qc)[Q][1 + DY + DX], const float (&e)[Q],
-                                           int (&cz)[Q], int (&cyz)[Q], int (&cxz)[Q]) {
+                                           const u64 (&qq)[Q][1 + DY + DX], const float (&e)[Q],
+                                           float (&cz)[Q], float (&cyz)[Q], float (&cxz)[Q]) {
     constexpr int D = 1 + DY + DX;
 #pragma unroll 1
     for (int j = 0; j < n4; ++j) {
-        float4 r[D];
-#pragma unroll
-        for (int c = 0; c < D; ++c) r[c] = *reinterpret_cast<const float4*>(s + c * ldt + 4 * j);
+        ulonglong2 r[D];
+        load_refs4<D>(s, ldt, j, r);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            count_one<DY, DX, Q, 0>(qc[q], r, e[q], cz[q], cyz[q], cxz[q]);
-            count_one<DY, DX, Q, 1>(qc[q], r, e[q], cz[q], cyz[q], cxz[q]);
-            count_one<DY, DX, Q, 2>(qc[q], r, e[q], cz[q], cyz[q], cxz[q]);
-            count_one<DY, DX, Q, 3>(qc[q], r, e[q], cz[q], cyz[q], cxz[q]);
+            float dx[D], dy[D], dz[D], dw[D];
+            diff4<D>(qq[q], r, dx, dy, dz, dw);
+            count_one<DY, DX>(dx, e[q], cz[q], cyz[q], cxz[q]);
+            count_one<DY, DX>(dy, e[q], cz[q], cyz[q], cxz[q]);
+            count_one<DY, DX>(dz, e[q], cz[q], cyz[q], cxz[q]);
+            count_one<DY, DX>(dw, e[q], cz[q], cyz[q], cxz[q]);
         }
     }
 }

@@ -59,14 +59,14 @@ template <int D, int KS>
 __global__ void __launch_bounds__(kUnitThreads) knn_exact_kernel(const float* __restrict__ pts, int N,
                                                                  int ld, int k, float* __restrict__ eps) {
     __shared__ __align__(16) float s[D * kUnitTile];
-    float qc[kUnitQ][D];
+    u64 qq[kUnitQ][D];
     float t[kUnitQ][KS];
     const int i0 = blockIdx.x * (kUnitThreads * kUnitQ) + threadIdx.x;
 #pragma unroll
     for (int q = 0; q < kUnitQ; ++q) {
         const int i = i0 + q * kUnitThreads;
 #pragma unroll
-        for (int c = 0; c < D; ++c) qc[q][c] = i < N ? pts[(size_t)c * ld + i] : 0.0f;
+        for (int c = 0; c < D; ++c) qq[q][c] = dup2(i < N ? pts[(size_t)c * ld + i] : 0.0f);
 #pragma unroll
         for (int m = 0; m < KS; ++m) t[q][m] = f_inf();
     }
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kUnitThreads) knn_exact_kernel(const float* __
         stage_soa<D>(pts, ld, N, base, s);
         __syncthreads();
         const int nv = min(kUnitTile, N - base);
-        knn_tile<D, kUnitQ, KS>(s, kUnitTile, (nv + 3) >> 2, qc, t);
+        knn_tile<D, kUnitQ, KS>(s, kUnitTile, (nv + 3) >> 2, qq, t);
     }
 #pragma unroll
     for (int q = 0; q < kUnitQ; ++q) {
@@ -169,33 +169,33 @@ __global__ void __launch_bounds__(kUnitThreads) count_exact_kernel(const float* 
                                                                    int32_t* __restrict__ counts) {
     constexpr int D = 1 + DY + DX;
     __shared__ __align__(16) float s[D * kUnitTile];
-    float qc[kUnitQ][D];
+    u64 qq[kUnitQ][D];
     float e[kUnitQ];
-    int cz[kUnitQ], cyz[kUnitQ], cxz[kUnitQ];
+    float cz[kUnitQ], cyz[kUnitQ], cxz[kUnitQ];
     const int i0 = blockIdx.x * (kUnitThreads * kUnitQ) + threadIdx.x;
 #pragma unroll
     for (int q = 0; q < kUnitQ; ++q) {
         const int i = i0 + q * kUnitThreads;
 #pragma unroll
-        for (int c = 0; c < D; ++c) qc[q][c] = i < N ? pts[(size_t)c * ld + i] : 0.0f;
+        for (int c = 0; c < D; ++c) qq[q][c] = dup2(i < N ? pts[(size_t)c * ld + i] : 0.0f);
         e[q] = i < N ? eps[i] : 0.0f;
-        cz[q] = cyz[q] = cxz[q] = 0;
+        cz[q] = cyz[q] = cxz[q] = 0.0f;
     }
     for (int base = 0; base < N; base += kUnitTile) {
         __syncthreads();
         stage_soa<D>(pts, ld, N, base, s);
         __syncthreads();
         const int nv = min(kUnitTile, N - base);
-        count_tile<DY, DX, kUnitQ>(s, kUnitTile, (nv + 3) >> 2, qc, e, cz, cyz, cxz);
+        count_tile<DY, DX, kUnitQ>(s, kUnitTile, (nv + 3) >> 2, qq, e, cz, cyz, cxz);
     }
 #pragma unroll
     for (int q = 0; q < kUnitQ; ++q) {
         const int i = i0 + q * kUnitThreads;
         if (i < N) {
             const int self = e[q] > 0.0f ? 1 : 0;  // the point itself lies at distance 0
-            counts[i] = cz[q] - self;
-            counts[(size_t)N + i] = cyz[q] - self;
-            counts[(size_t)2 * N + i] = cxz[q] - self;
+            counts[i] = (int)cz[q] - self;
+            counts[(size_t)N + i] = (int)cyz[q] - self;
+            counts[(size_t)2 * N + i] = (int)cxz[q] - self;
         }
     }
 }
