@@ -216,6 +216,9 @@ def bench_ours(args):
             return te.te_surrogate_test(h, series_dev, w.t_starts[0], w.window, w.S, w.k, out=outs)
         return te.te_estimate(h, series_dev, w.instances, w.k, te=outs)
 
+    tuned = None
+    if not args.no_autotune:
+        tuned = te.te_autotune(h, ds, w.instances, w.k)
     outs = None
     if surrogate:
         nt = len(w.t_starts[0])
@@ -342,6 +345,7 @@ def bench_ours(args):
     if not args.no_per_launch:
         if surrogate:
             n_t_sub = max(1, min(len(w.t_starts[0]), args.per_launch_instances // (w.S + 1)))
+            n_t_sub = max(1, min(n_t_sub, int(2.0e12 // max(1, lane_ops(w) // len(w.t_starts[0])))))
             wsub = I.Workload(w.name, w.series, w.instances[: n_t_sub * (w.S + 1)], w.k,
                               [w.t_starts[0][:n_t_sub]], w.window, w.S)
         else:
@@ -388,7 +392,9 @@ def bench_ours(args):
         "config": {"workload": spec["desc"], "estimates_per_step": n_est,
                    "pair_evals_per_step": pe_step, "k": w.k,
                    "l2": "256 MiB buffer written between timed steps (inputs smaller than L2)",
-                   "per_rank": "every rank runs the full workload (weak scaling)"},
+                   "per_rank": "every rank runs the full workload (weak scaling)",
+                   "launch_shape": None if tuned is None else {"threads": tuned[0], "queries_per_thread": tuned[1],
+                                                               "chosen_by": "te_autotune"}},
         "te_estimates_per_s": te_rate,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks, "per_launch": per,
@@ -447,6 +453,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c3")
     ap.add_argument("--per-launch-instances", type=int, default=2002)
     ap.add_argument("--no-per-launch", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-instances", type=int, default=32)

@@ -172,6 +172,21 @@ int32_t te_last_launch_count(const te_handle* h);
  * thread (2 or 4) or 0 for automatic. Takes effect on the next te_estimate call. */
 te_status te_set_launch_config(te_handle* h, int32_t threads, int32_t qpt);
 
+/* te_autotune - choose the batched kernel's launch shape (CTA size, queries per thread) for a
+ * batch by measurement. The paper fixes 512 threads per block (Implementation, "Low-level
+ * implementation details"); here candidates are timed on a cost-stratified subset of the batch
+ * (about eight waves of work items; candidates whose padded query slots exceed the minimum by more
+ * than 1/8 are skipped) and the fastest is kept in the handle for every later batch with the same
+ * signature (embedding dimensions, k, point count). Results do not depend on the shape.
+ *   inst        the batch as for te_estimate (or the instances te_surrogate_test would build).
+ *   cache_path  nullable: a JSON file read before tuning (a cached signature skips the timing)
+ *               and rewritten with the handle's entries after tuning.
+ *   threads_out, qpt_out  nullable: the shape now in effect for this signature.
+ * Synchronises the stream. Launch-config overrides (te_set_launch_config) take precedence. */
+te_status te_autotune(te_handle* h, const te_series* series, int32_t n_series, const te_instance* inst,
+                      int32_t n_inst, int32_t k, const char* cache_path, int32_t* threads_out,
+                      int32_t* qpt_out, void* stream);
+
 /* Batching mode of te_estimate / te_surrogate_test. per_instance = 0 (default): one persistent
  * launch for the whole batch, captured in a CUDA graph. per_instance = 1: the same kernel and
  * tables, launched once per instance with a grid of that instance's work items and no graph,

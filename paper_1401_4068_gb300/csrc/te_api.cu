@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -135,6 +136,7 @@ struct te_handle {
     bool profiling = false, ev_recorded = false;
     int last_launches = 0;
     int cfg_threads = 0, cfg_qpt = 0;
+    std::map<std::string, std::pair<int, int>> tuned;  // batch signature -> (threads, qpt)
     bool per_instance = false;  // one launch per instance instead of one persistent launch
 
     DevBuf<InstDesc> d_insts;
@@ -223,6 +225,24 @@ te_status validate_series(te_handle* h, const te_series* series, int n_series) {
 // k > 4, where 4 would not fit the register budget), and for a uniform point count the CTA size
 // with the fewest padded query slots, ties to the smallest CTA of at least 128 threads (several
 // CTAs per SM hide the per-item barriers)
+// Signature of a batch for the autotuner's cache: embedding dimensions, top-k slots and the
+// point count (exact when uniform, else the power-of-two bucket of the largest).
+std::string shape_signature(const std::vector<InstDesc>& insts, int ks) {
+    int dlo = 99, dhi = 0, nmax = 0;
+    bool uniform = true;
+    for (const auto& I : insts) {
+        dlo = std::min(dlo, I.d);
+        dhi = std::max(dhi, I.d);
+        nmax = std::max(nmax, I.N);
+        uniform &= I.N == insts[0].N;
+    }
+    int bucket = 1;
+    while (bucket < nmax) bucket <<= 1;
+    char buf[96];
+    snprintf(buf, sizeof buf, "d%d-%d_ks%d_%s%d", dlo, dhi, ks, uniform ? "N" : "Nmax", uniform ? nmax : bucket);
+    return buf;
+}
+
 void choose_shape(te_handle* h, const std::vector<InstDesc>& insts, int ks, int* threads, int* qpt) {
     int dmax = 1;
     for (const auto& I : insts) dmax = std::max(dmax, I.d);
@@ -232,6 +252,14 @@ void choose_shape(te_handle* h, const std::vector<InstDesc>& insts, int ks, int*
     if (h->cfg_threads) {
         *threads = h->cfg_threads;
         return;
+    }
+    if (!h->cfg_qpt) {
+        auto it = h->tuned.find(shape_signature(insts, ks));
+        if (it != h->tuned.end()) {
+            *threads = it->second.first;
+            *qpt = it->second.second;
+            return;
+        }
     }
     bool uniform = true;
     for (const auto& I : insts) uniform &= (I.N == insts[0].N);
@@ -703,6 +731,152 @@ TE_EXPORT te_status te_surrogate_test(te_handle* h, const te_series* series, int
     if ((st = build_plan(h, series, n_series, inst.data(), (int)inst.size(), k, &P)) != TE_OK) return st;
     return run_batched(h, P, series, n_series, inst.data(), (int)inst.size(), k, nullptr, nullptr, nullptr,
                        nullptr, n_series * n_t, S, te_orig, te_surr, p, static_cast<cudaStream_t>(stream));
+}
+
+namespace {
+
+bool load_tune_cache(te_handle* h, const char* path) {
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char line[512], key[128];
+    int t = 0, q = 0;
+    while (fgets(line, sizeof line, f)) {
+        if (sscanf(line, " \"%127[^\"]\": {\"threads\": %d, \"qpt\": %d", key, &t, &q) == 3 && t >= 64 &&
+            t <= te::kBatchedMaxThreads && t % 32 == 0 && (q == 2 || q == 4))
+            h->tuned[key] = {t, q};
+    }
+    fclose(f);
+    return true;
+}
+
+bool save_tune_cache(te_handle* h, const char* path, const std::map<std::string, float>& ms) {
+    std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "w");
+    if (!f) return false;
+    fprintf(f, "{\n");
+    size_t n = 0;
+    for (const auto& kv : h->tuned) {
+        auto it = ms.find(kv.first);
+        fprintf(f, " \"%s\": {\"threads\": %d, \"qpt\": %d, \"ms\": %.4f}%s\n", kv.first.c_str(), kv.second.first,
+                kv.second.second, it == ms.end() ? -1.0 : (double)it->second, ++n < h->tuned.size() ? "," : "");
+    }
+    fprintf(f, "}\n");
+    fclose(f);
+    return rename(tmp.c_str(), path) == 0;
+}
+
+}  // namespace
+
+TE_EXPORT te_status te_autotune(te_handle* h, const te_series* series, int32_t n_series, const te_instance* inst,
+                                int32_t n_inst, int32_t k, const char* cache_path, int32_t* threads_out,
+                                int32_t* qpt_out, void* stream) {
+    if (!h) return TE_EINVAL;
+    h->err.clear();
+    if (k < 1 || k > kMaxK) return h->fail(TE_EINVAL, "te_autotune: k=%d outside 1..%d", k, kMaxK);
+    if (n_inst < 1 || !inst) return h->fail(TE_EINVAL, "te_autotune: no instances");
+    te_status st = validate_series(h, series, n_series);
+    if (st != TE_OK) return st;
+    DeviceGuard g(h->device);
+    cudaStream_t strm = static_cast<cudaStream_t>(stream);
+    const int save_t = h->cfg_threads, save_q = h->cfg_qpt;
+    const bool save_prof = h->profiling;
+    auto restore = [&]() {
+        h->cfg_threads = save_t;
+        h->cfg_qpt = save_q;
+        h->profiling = save_prof;
+    };
+    h->cfg_threads = h->cfg_qpt = 0;
+    Plan P;
+    if ((st = build_plan(h, series, n_series, inst, n_inst, k, &P)) != TE_OK) {
+        restore();
+        return st;
+    }
+    const int ks = P.var.ks;
+    const std::string sig = shape_signature(P.insts, ks);
+    if (cache_path && cache_path[0]) load_tune_cache(h, cache_path);
+    std::map<std::string, float> best_ms;
+    auto found = h->tuned.find(sig);
+    if (found == h->tuned.end()) {
+        // a cost-stratified subset of about eight waves of the default plan's work items
+        std::vector<int> order(n_inst);
+        for (int i = 0; i < n_inst; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            const InstDesc &A = P.insts[a], &B = P.insts[b];
+            return (double)A.N * A.N * (1 + 2 * A.d) > (double)B.N * B.N * (1 + 2 * B.d);
+        });
+        const int64_t want_items = 8LL * P.grid;
+        const int stride = (int)std::max<int64_t>(1, (int64_t)P.items.size() / std::max<int64_t>(1, want_items));
+        std::vector<te_instance> sub;
+        for (int i = 0; i < n_inst; i += stride) sub.push_back(inst[order[i]]);
+        int dmax = 1;
+        for (const auto& I : P.insts) dmax = std::max(dmax, I.d);
+        std::vector<int> qs = (ks == 5 && dmax <= 4) ? std::vector<int>{4, 2} : std::vector<int>{2};
+        bool uniform = true;
+        for (const auto& I : P.insts) uniform &= I.N == P.insts[0].N;
+        bool grew = false;
+        cudaError_t e = h->d_te_all.ensure(sub.size(), &grew);
+        if (e != cudaSuccess) {
+            restore();
+            return h->fail(TE_ENOMEM, "te_autotune: %s", cudaGetErrorString(e));
+        }
+        if (grew) ++h->workspace_gen;
+        float best = 1e30f;
+        int bt = 0, bq = 0;
+        h->profiling = true;
+        for (int q : qs) {
+            int64_t min_slots = INT64_MAX;
+            if (uniform)
+                for (int t = 64; t <= te::kBatchedMaxThreads; t += 32) {
+                    const int64_t per = (int64_t)t * q;
+                    min_slots = std::min(min_slots, ((P.insts[0].N + per - 1) / per) * per);
+                }
+            for (int t = 64; t <= te::kBatchedMaxThreads; t += 32) {
+                if (uniform) {
+                    const int64_t per = (int64_t)t * q;
+                    if (((P.insts[0].N + per - 1) / per) * per > min_slots + min_slots / 8) continue;
+                } else if (t % 64) {
+                    continue;
+                }
+                h->cfg_threads = t;
+                h->cfg_qpt = q;
+                Plan S;
+                if (build_plan(h, series, n_series, sub.data(), (int)sub.size(), k, &S) != TE_OK) continue;
+                float med = 0;
+                std::vector<float> v;
+                for (int rep = 0; rep < 4; ++rep) {
+                    if (run_batched(h, S, series, n_series, sub.data(), (int)sub.size(), k, h->d_te_all.p, nullptr,
+                                    nullptr, nullptr, 0, 0, nullptr, nullptr, nullptr, strm) != TE_OK)
+                        break;
+                    float ms = 0;
+                    if (cudaEventSynchronize(h->ev1) != cudaSuccess ||
+                        cudaEventElapsedTime(&ms, h->ev0, h->ev1) != cudaSuccess)
+                        break;
+                    if (rep > 0) v.push_back(ms);  // the first run captures the graph
+                }
+                if (v.size() == 3) {
+                    std::sort(v.begin(), v.end());
+                    med = v[1];
+                    if (med < best) {
+                        best = med;
+                        bt = t;
+                        bq = q;
+                    }
+                }
+            }
+        }
+        restore();
+        h->err.clear();
+        if (!bt) return h->fail(TE_ECUDA, "te_autotune: no candidate ran");
+        h->tuned[sig] = {bt, bq};
+        best_ms[sig] = best;
+        if (cache_path && cache_path[0] && !save_tune_cache(h, cache_path, best_ms))
+            return h->fail(TE_EINVAL, "te_autotune: cannot write %s", cache_path);
+        found = h->tuned.find(sig);
+    }
+    restore();
+    if (threads_out) *threads_out = found->second.first;
+    if (qpt_out) *qpt_out = found->second.second;
+    return TE_OK;
 }
 
 TE_EXPORT te_status te_set_profiling(te_handle* h, int32_t enable) {

@@ -28,7 +28,7 @@ _STATUS = {0: "TE_OK", 1: "TE_EINVAL", 2: "TE_ERANGE", 3: "TE_ENOMEM", 4: "TE_EC
 EXPORTS = ["te_create", "te_destroy", "te_last_error", "te_sync_status", "te_embed",
            "te_knn_maxnorm", "te_range_count", "te_estimate", "te_surrogate_test",
            "te_set_profiling", "te_last_kernel_ms", "te_last_launch_count", "te_set_launch_config",
-           "te_set_batching", "te_surrogate_test_static"]
+           "te_set_batching", "te_surrogate_test_static", "te_autotune"]
 
 
 class TEError(RuntimeError):
@@ -89,9 +89,11 @@ def load() -> C.CDLL:
     lib.te_last_launch_count.argtypes = [P]
     lib.te_set_launch_config.argtypes = [P, i32, i32]
     lib.te_set_batching.argtypes = [P, i32]
+    lib.te_autotune.argtypes = [P, C.POINTER(te_series), i32, C.POINTER(te_instance), i32, i32,
+                                C.c_char_p, C.POINTER(i32), C.POINTER(i32), P]
     for name in ("te_sync_status", "te_embed", "te_knn_maxnorm", "te_range_count", "te_estimate",
                  "te_surrogate_test", "te_set_profiling", "te_last_kernel_ms",
-                 "te_last_launch_count", "te_set_launch_config", "te_set_batching"):
+                 "te_last_launch_count", "te_set_launch_config", "te_set_batching", "te_autotune"):
         getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -309,3 +311,19 @@ def te_set_launch_config(h: Handle, threads: int = 0, qpt: int = 0):
 
 def te_set_batching(h: Handle, per_instance: bool):
     h.check(h.lib.te_set_batching(h.h, 1 if per_instance else 0))
+
+
+def te_autotune(h: Handle, series: Sequence[DeviceSeries], instances: Sequence, k: int,
+                cache_path: Optional[str] = None, stream=None):
+    """Measure and keep the batched kernel's launch shape for this batch signature.
+    Returns (threads, queries_per_thread)."""
+    ser = _series_array(series)
+    n = len(instances)
+    ins = (te_instance * max(1, n))()
+    for i, it in enumerate(instances):
+        ins[i] = te_instance(int(it.series), int(it.t_start), int(it.window), int(it.perm))
+    t, q = C.c_int32(), C.c_int32()
+    h.check(h.lib.te_autotune(h.h, ser, len(series), ins, n, int(k),
+                              None if cache_path is None else cache_path.encode(),
+                              C.byref(t), C.byref(q), _stream(stream)))
+    return int(t.value), int(q.value)

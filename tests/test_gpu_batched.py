@@ -236,3 +236,28 @@ def test_per_instance_launch_mode_is_bit_identical(te_handle):
     assert n == len(w.instances) + 1
     assert torch.equal(ref["counts"], got["counts"]) and torch.equal(ref["eps"], got["eps"])
     assert torch.equal(ref["te"], got["te"])
+
+
+def test_autotune_picks_a_shape_caches_it_and_keeps_results(te_handle, tmp_path):
+    w = I.config(3, n_t=2, S=60)
+    ds = te.to_device(w.series)
+    ref = te.te_estimate(te_handle, ds, w.instances, w.k, want_counts=True)
+    cache = str(tmp_path / "tune.json")
+    h2 = te.Handle(0)
+    try:
+        t, q = te.te_autotune(h2, ds, w.instances, w.k, cache_path=cache)
+        assert t % 32 == 0 and 64 <= t <= 512 and q in (2, 4)
+        got = te.te_estimate(h2, ds, w.instances, w.k, want_counts=True)
+        torch.cuda.synchronize()
+        assert torch.equal(ref["counts"], got["counts"]) and torch.equal(ref["eps"], got["eps"])
+        assert torch.max(torch.abs(ref["te"] - got["te"])).item() <= 1e-9
+        import json
+        entries = json.load(open(cache))
+        assert any(v["threads"] == t and v["qpt"] == q for v in entries.values())
+    finally:
+        h2.close()
+    h3 = te.Handle(0)  # a fresh handle reads the cache instead of timing again
+    try:
+        assert te.te_autotune(h3, ds, w.instances, w.k, cache_path=cache) == (t, q)
+    finally:
+        h3.close()
