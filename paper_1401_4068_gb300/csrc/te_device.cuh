@@ -31,18 +31,6 @@ __device__ __forceinline__ void topk_push(float (&t)[KS], float x) {
     }
 }
 
-// The same insertion decided once per warp: the network leaves the list unchanged for lanes
-// whose x is not below their largest slot (min(t[KS-1], x) = t[KS-1]), so it can run for the
-// whole warp whenever any lane needs it. The branch is warp-uniform. All 32 lanes must call it.
-template <int KS>
-__device__ __forceinline__ void topk_push_warp(float (&t)[KS], float x) {
-    if (__any_sync(0xffffffffu, x < t[KS - 1])) {
-#pragma unroll
-        for (int s = KS - 1; s > 0; --s) t[s] = fmaxf(t[s - 1], fminf(t[s], x));
-        t[0] = fminf(t[0], x);
-    }
-}
-
 // slot k of the ascending list (k is a runtime value < KS), written as the maximum of slots
 // 0..k so that the list stays in registers (a select on s == k is compiled as a dynamic index)
 template <int KS>
@@ -124,7 +112,7 @@ __device__ __forceinline__ void load_refs4(const float* __restrict__ s, int ldt,
 // Pass 1 over one staged reference tile: smem holds coordinate c of reference j at
 // s[c * ldt + j] (structure of arrays, +inf past the last valid reference). Every thread
 // streams the whole tile against its Q register-resident queries; four references are
-// read per 128-bit broadcast load. Called by whole warps (top-k insertion is warp-uniform).
+// read per 128-bit broadcast load.
 // ---------------------------------------------------------------------------------------
 template <int D, int Q, int KS>
 __device__ __forceinline__ void knn_tile(const float* __restrict__ s, int ldt, int n4,
@@ -137,10 +125,10 @@ __device__ __forceinline__ void knn_tile(const float* __restrict__ s, int ldt, i
         for (int q = 0; q < Q; ++q) {
             float dx[D], dy[D], dz[D], dw[D];
             diff4<D>(qq[q], r, dx, dy, dz, dw);
-            topk_push_warp(t[q], absmax_range<0, D - 1>(dx));
-            topk_push_warp(t[q], absmax_range<0, D - 1>(dy));
-            topk_push_warp(t[q], absmax_range<0, D - 1>(dz));
-            topk_push_warp(t[q], absmax_range<0, D - 1>(dw));
+            topk_push(t[q], absmax_range<0, D - 1>(dx));
+            topk_push(t[q], absmax_range<0, D - 1>(dy));
+            topk_push(t[q], absmax_range<0, D - 1>(dz));
+            topk_push(t[q], absmax_range<0, D - 1>(dw));
         }
     }
 }
