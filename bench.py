@@ -48,7 +48,21 @@ WORKLOADS = {
     "c4": dict(cid=4, kw={}, desc="C4 uneven MEG-like batch: 20 pink-noise pairs x 30 t, N 50..10000, D 3..11"),
     "c5": dict(cid=5, kw={}, desc="C5 large ensemble: N=12000, D=11, 200 t x (1+200) = 40,200 estimates"),
     "c5-small": dict(cid=5, kw=dict(n_t=2, S=20), desc="C5 shapes, 2 time points x (1+20)"),
+    "ar1-scan": dict(cid=None, kw={}, desc="AR(1) unidirectional scenario (Table 1): 50 trials x 3000 samples, "
+                     "d=1, windows of 300 (N=15000, D=3) at 0.2/0.5/0.8/1.1 s, delay scan u=1..20, "
+                     "500 surrogates each = 40,080 estimates, k=4"),
 }
+
+
+def load_workload(spec):
+    from paper_1401_4068_gb300 import inputs as I
+    if spec["cid"] is None:
+        return I.ar1_analysis("unidirectional", S=500)
+    return I.config(spec["cid"], **spec["kw"])
+
+
+def scan_range(w):
+    return (w.extra["u_lo"], w.extra["u_hi"]) if "u_lo" in w.extra else None
 
 
 def dist_env():
@@ -58,14 +72,21 @@ def dist_env():
     return ws, rank, local
 
 
+def _scan_factor(w):
+    sr = scan_range(w)
+    return 1 if sr is None else sr[1] - sr[0] + 1
+
+
 def pair_evals(w):
-    """Ordered pairs i != j of ONE pass, summed over instances."""
-    return sum(w.n_points(i) * (w.n_points(i) - 1) for i in w.instances)
+    """Ordered pairs i != j of ONE pass, summed over the estimates of one step (a delay scan
+    repeats every listed estimate once per scanned delay)."""
+    return _scan_factor(w) * sum(w.n_points(i) * (w.n_points(i) - 1) for i in w.instances)
 
 
 def lane_ops(w):
     """Algorithmic FP32 operations of both passes: D subtractions + D abs-max per ordered pair."""
-    return 2 * sum(w.n_points(i) * (w.n_points(i) - 1) * 2 * w.joint_dim(i) for i in w.instances)
+    return 2 * _scan_factor(w) * sum(w.n_points(i) * (w.n_points(i) - 1) * 2 * w.joint_dim(i)
+                                     for i in w.instances)
 
 
 def kernel_source_hash() -> str:
@@ -205,13 +226,17 @@ def bench_ours(args):
         dist.init_process_group("nccl", device_id=dev)
     build.build()
     spec = WORKLOADS[args.workload]
-    w = I.config(spec["cid"], **spec["kw"])
+    w = load_workload(spec)
+    scan = scan_range(w)
     surrogate = w.S > 0 and w.t_starts is not None
     h = te.Handle(local)
     ds = te.to_device(w.series, dev)
     te.te_set_profiling(h, True)
 
     def step(series_dev, outs=None):
+        if scan:
+            return te.te_delay_scan(h, series_dev[0], w.t_starts[0], w.window, scan[0], scan[1], w.S, w.k,
+                                    out=outs)
         if surrogate:
             return te.te_surrogate_test(h, series_dev, w.t_starts[0], w.window, w.S, w.k, out=outs)
         return te.te_estimate(h, series_dev, w.instances, w.k, te=outs)
@@ -220,7 +245,13 @@ def bench_ours(args):
     if not args.no_autotune:
         tuned = te.te_autotune(h, ds, w.instances, w.k)
     outs = None
-    if surrogate:
+    if scan:
+        n_u = scan[1] - scan[0] + 1
+        nt = len(w.t_starts[0])
+        outs = {"te": torch.empty((n_u, nt), dtype=torch.float64, device=dev),
+                "p": torch.empty((n_u, nt), dtype=torch.float64, device=dev),
+                "u_best": torch.empty(nt, dtype=torch.int32, device=dev)}
+    elif surrogate:
         nt = len(w.t_starts[0])
         outs = {"te_orig": torch.empty((1, nt), dtype=torch.float64, device=dev),
                 "te_surr": torch.empty((1, nt, w.S), dtype=torch.float64, device=dev),
@@ -267,7 +298,7 @@ def bench_ours(args):
     te.te_sync_status(h)
 
     pe_step = 2 * pair_evals(w)
-    n_est = len(w.instances)
+    n_est = len(w.instances) * _scan_factor(w)
     value = ws * pe_step * args.steps / (total_ms / 1e3)
     te_rate = ws * n_est * args.steps / (total_ms / 1e3)
 
@@ -298,11 +329,11 @@ def bench_ours(args):
               "perms": None if s.perms is None else _t.from_numpy(np.ascontiguousarray(s.perms)).pin_memory()}
         host.append(hs)
     h2d = sum(v.numel() * v.element_size() for hs in host for v in hs.values() if v is not None)
-    if surrogate:
+    if isinstance(outs, dict):
         out_host = {k: _t.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in outs.items()}
     else:
         out_host = _t.empty(outs.shape, dtype=outs.dtype).pin_memory()
-    d2h = (sum(v.numel() * v.element_size() for v in out_host.values()) if surrogate
+    d2h = (sum(v.numel() * v.element_size() for v in out_host.values()) if isinstance(outs, dict)
            else out_host.numel() * out_host.element_size())
 
     def e2e_step():
@@ -312,7 +343,7 @@ def bench_ours(args):
             if hs["perms"] is not None:
                 s.perms.copy_(hs["perms"], non_blocking=True)
         step(ds, outs)
-        if surrogate:
+        if isinstance(outs, dict):
             for k in outs:
                 out_host[k].copy_(outs[k], non_blocking=True)
         else:
@@ -344,14 +375,21 @@ def bench_ours(args):
     per = None
     if not args.no_per_launch:
         if surrogate:
-            n_t_sub = max(1, min(len(w.t_starts[0]), args.per_launch_instances // (w.S + 1)))
-            n_t_sub = max(1, min(n_t_sub, int(2.0e12 // max(1, lane_ops(w) // len(w.t_starts[0])))))
+            per_t = lane_ops(w) // len(w.t_starts[0])
+            n_t_sub = max(1, min(len(w.t_starts[0]), args.per_launch_instances // ((w.S + 1) * _scan_factor(w))))
+            n_t_sub = max(1, min(n_t_sub, int(2.0e12 // max(1, per_t))))
             wsub = I.Workload(w.name, w.series, w.instances[: n_t_sub * (w.S + 1)], w.k,
-                              [w.t_starts[0][:n_t_sub]], w.window, w.S)
+                              [w.t_starts[0][:n_t_sub]], w.window, w.S, extra=dict(w.extra))
+            if scan:  # a few delays of the first window keep the unbatched run short
+                n_u_sub = max(1, min(_scan_factor(w), args.per_launch_instances // (w.S + 1)))
+                wsub.extra = dict(u_lo=scan[0], u_hi=scan[0] + n_u_sub - 1)
         else:
             wsub = I.Workload(w.name, w.series, w.instances[: args.per_launch_instances], w.k)
 
         def sub_step(o=None):
+            if scan:
+                sr = scan_range(wsub)
+                return te.te_delay_scan(h, ds[0], wsub.t_starts[0], wsub.window, sr[0], sr[1], wsub.S, wsub.k)
             if surrogate:
                 return te.te_surrogate_test(h, ds, wsub.t_starts[0], wsub.window, wsub.S, wsub.k)
             return te.te_estimate(h, ds, wsub.instances, wsub.k)
@@ -372,7 +410,7 @@ def bench_ours(args):
             res[(mode, "launches")] = n_launch
         te.te_set_batching(h, False)
         pe_sub = 2 * pair_evals(wsub)
-        per = {"instances": len(wsub.instances),
+        per = {"instances": len(wsub.instances) * _scan_factor(wsub),
                "per_instance_launch": {"value": pe_sub / (res[True] / 1e3), "unit": "pair-evals/s",
                                        "te_estimates_per_s": len(wsub.instances) / (res[True] / 1e3),
                                        "ms": round(res[True], 3), "kernel_launches": res[(True, "launches")]},
@@ -417,7 +455,7 @@ def bench_reference(args):
     import oracle
     from paper_1401_4068_gb300 import inputs as I
     spec = WORKLOADS[args.workload]
-    w = I.config(spec["cid"], **spec["kw"])
+    w = load_workload(spec)
     threads = oracle.default_threads()
     per_step = max(threads, args.reference_instances)
     for s in range(args.warmup):

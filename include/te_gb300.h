@@ -172,6 +172,19 @@ int32_t te_last_launch_count(const te_handle* h);
  * thread (2 or 4) or 0 for automatic. Takes effect on the next te_estimate call. */
 te_status te_set_launch_config(te_handle* h, int32_t threads, int32_t qpt);
 
+/* te_delay_scan - delay reconstruction (Eq. 5, "Reconstruction of information transfer delays"):
+ * TE_SPO(X -> Y, t, u) for every scanned delay u = u_lo .. u_hi (the series' own u is not used)
+ * and every analysis start t_starts[j], each with S surrogates (perms[0 .. S-1]), all estimates
+ * in one batched launch as te_surrogate_test; the reconstructed delay of start j is the u of
+ * largest original TE (ties to the smaller u).
+ *   te      device float64 [n_u][n_t] original TE, n_u = u_hi - u_lo + 1
+ *   p       device float64 [n_u][n_t] p-values, or NULL (NaN values when S == 0)
+ *   u_best  device int32 [n_t]
+ * Every (u, t) must satisfy the embedding range of te_estimate (TE_ERANGE otherwise). */
+te_status te_delay_scan(te_handle* h, const te_series* series, const int32_t* t_starts, int32_t n_t,
+                        int32_t window, int32_t u_lo, int32_t u_hi, int32_t S, int32_t k, double* te,
+                        double* p, int32_t* u_best, void* stream);
+
 /* te_autotune - choose the batched kernel's launch shape (CTA size, queries per thread) for a
  * batch by measurement. The paper fixes 512 threads per block (Implementation, "Low-level
  * implementation details"); here candidates are timed on a cost-stratified subset of the batch

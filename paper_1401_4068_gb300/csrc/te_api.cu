@@ -142,7 +142,7 @@ struct te_handle {
     DevBuf<InstDesc> d_insts;
     DevBuf<WorkItem> d_items;
     DevBuf<int32_t> d_words;  // [0] queue head, [1] flags
-    DevBuf<double> d_partial, d_partial_abs, d_te_all;
+    DevBuf<double> d_partial, d_partial_abs, d_te_all, d_surr_ws, d_p_ws;
     DevBuf<float2> d_psi;
     HostBuf<unsigned char> h_stage;
     int workspace_gen = 0;
@@ -583,6 +583,8 @@ TE_EXPORT void te_destroy(te_handle* h) {
     h->d_partial.release();
     h->d_partial_abs.release();
     h->d_te_all.release();
+    h->d_surr_ws.release();
+    h->d_p_ws.release();
     h->d_psi.release();
     h->h_stage.release();
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -876,6 +878,49 @@ TE_EXPORT te_status te_autotune(te_handle* h, const te_series* series, int32_t n
     restore();
     if (threads_out) *threads_out = found->second.first;
     if (qpt_out) *qpt_out = found->second.second;
+    return TE_OK;
+}
+
+TE_EXPORT te_status te_delay_scan(te_handle* h, const te_series* series, const int32_t* t_starts, int32_t n_t,
+                                  int32_t window, int32_t u_lo, int32_t u_hi, int32_t S, int32_t k, double* te,
+                                  double* p, int32_t* u_best, void* stream) {
+    if (!h) return TE_EINVAL;
+    h->err.clear();
+    if (k < 1 || k > kMaxK) return h->fail(TE_EINVAL, "te_delay_scan: k=%d outside 1..%d", k, kMaxK);
+    if (!series || !t_starts || n_t < 1 || window < 1 || S < 0 || !te || !u_best)
+        return h->fail(TE_EINVAL, "te_delay_scan: null output, n_t=%d, window=%d or S=%d", n_t, window, S);
+    if (u_lo < 0 || u_hi < u_lo) return h->fail(TE_EINVAL, "te_delay_scan: u range %d..%d", u_lo, u_hi);
+    te_status st = validate_series(h, series, 1);
+    if (st != TE_OK) return st;
+    if (series->S < S) return h->fail(TE_EINVAL, "te_delay_scan: series has %d permutations < S=%d", series->S, S);
+    const int n_u = u_hi - u_lo + 1;
+    const int64_t n_inst64 = (int64_t)n_u * n_t * (S + 1);
+    if (n_inst64 > INT32_MAX / 4) return h->fail(TE_ENOTIMPL, "te_delay_scan: too many estimates");
+    // one series descriptor per scanned delay (same data), estimates grouped per (u, t)
+    std::vector<te_series> ser((size_t)n_u, *series);
+    for (int iu = 0; iu < n_u; ++iu) ser[iu].u = u_lo + iu;
+    std::vector<te_instance> inst;
+    inst.reserve((size_t)n_inst64);
+    for (int iu = 0; iu < n_u; ++iu)
+        for (int j = 0; j < n_t; ++j)
+            for (int m = -1; m < S; ++m) inst.push_back(te_instance{iu, t_starts[j], window, m});
+    DeviceGuard g(h->device);
+    Plan P;
+    if ((st = build_plan(h, ser.data(), n_u, inst.data(), (int)inst.size(), k, &P)) != TE_OK) return st;
+    const int n_groups = n_u * n_t;
+    bool grew = false;
+    cudaError_t e;
+    if ((S > 0 && (e = h->d_surr_ws.ensure((size_t)n_groups * S, &grew)) != cudaSuccess) ||
+        (!p && (e = h->d_p_ws.ensure((size_t)n_groups, &grew)) != cudaSuccess))
+        return h->fail(TE_ENOMEM, "te_delay_scan workspace: %s", cudaGetErrorString(e));
+    if (grew) ++h->workspace_gen;
+    cudaStream_t strm = static_cast<cudaStream_t>(stream);
+    st = run_batched(h, P, ser.data(), n_u, inst.data(), (int)inst.size(), k, nullptr, nullptr, nullptr, nullptr,
+                     n_groups, S, te, S > 0 ? h->d_surr_ws.p : nullptr, p ? p : h->d_p_ws.p, strm);
+    if (st != TE_OK) return st;
+    if ((e = te::launch_delay_argmax(te, n_u, n_t, u_lo, u_best, strm)) != cudaSuccess)
+        return h->cuda_fail(e, "delay argmax");
+    h->last_launches += 1;
     return TE_OK;
 }
 

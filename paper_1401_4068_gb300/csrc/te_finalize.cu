@@ -51,7 +51,30 @@ __global__ void finalize_groups_kernel(const double* __restrict__ te_all, int S,
     }
 }
 
+// Eq. 5: the reconstructed delay of each analysis start is the scanned u of largest TE
+// (strictly larger wins, so ties go to the smaller u; NaN never wins)
+__global__ void delay_argmax_kernel(const double* __restrict__ te, int n_u, int n_t, int u_lo,
+                                    int32_t* __restrict__ u_best) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_t) return;
+    double best = te[j];
+    int bu = 0;
+    for (int iu = 1; iu < n_u; ++iu) {
+        const double v = te[(size_t)iu * n_t + j];
+        if (v > best || (best != best && v == v)) {
+            best = v;
+            bu = iu;
+        }
+    }
+    u_best[j] = u_lo + bu;
+}
+
 }  // namespace
+
+cudaError_t launch_delay_argmax(const double* te, int n_u, int n_t, int u_lo, int32_t* u_best, cudaStream_t s) {
+    delay_argmax_kernel<<<(n_t + 127) / 128, 128, 0, s>>>(te, n_u, n_t, u_lo, u_best);
+    return cudaGetLastError();
+}
 
 const void* batched_kernel_ptr(const BatchedVariant& v) {
     if (v.dlo == v.dhi) {

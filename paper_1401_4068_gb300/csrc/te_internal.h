@@ -68,6 +68,7 @@ cudaError_t launch_batched(const BatchedVariant& v, const BatchArgs& a, int grid
 cudaError_t launch_finalize_te(const InstDesc* insts, int n_inst, const double* partial,
                                const double* partial_abs, double psi_k, double err_coef,
                                double* te, double* err, cudaStream_t s);
+cudaError_t launch_delay_argmax(const double* te, int n_u, int n_t, int u_lo, int32_t* u_best, cudaStream_t s);
 cudaError_t launch_finalize_groups(const double* te_all, int n_groups, int S, double* te_orig,
                                    double* te_surr, double* p, cudaStream_t s);
 

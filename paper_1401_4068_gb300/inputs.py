@@ -192,6 +192,54 @@ def gaussian_pair_iid(rng: np.random.Generator, R: int, T: int, rho: float):
     return x.astype(np.float32), y.astype(np.float32)
 
 
+# Table 1: parameters of the three coupled AR(1) scenarios (Eq. 12 - Eq. 16); delays in samples
+# (1 kHz sampling, so samples = ms), t counted from the first kept sample of a trial.
+AR1_SCENARIOS = {
+    "unidirectional": dict(ax=0.75, ay=0.35, byx=0.0, bxy=-0.35, dyx=0, dxy=10),
+    "two-step": dict(ax=0.75, ay=0.35, byx=0.0, bxy=-0.35, dyx=0, dxy=10),
+    "bidirectional": dict(ax=0.475, ay=0.35, byx=-0.4, bxy=-0.35, dyx=20, dxy=10),
+}
+
+
+def ar1_couplings(name: str, t: np.ndarray):
+    """gamma_XY(t), gamma_YX(t) of Eq. 14 - Eq. 16 (tanh ramps, slope 0.05, scaled to 0..1)."""
+    p = AR1_SCENARIOS[name]
+    ramp = lambda t0: 0.5 * (1.0 + np.tanh(0.05 * (t - t0)))
+    if name == "two-step":
+        gxy = p["bxy"] * 0.5 * (ramp(1000.0) + ramp(2000.0))
+    else:
+        gxy = p["bxy"] * ramp(1000.0)
+    gyx = p["byx"] * ramp(2000.0)
+    return gxy, gyx
+
+
+def ar1_scenario(rng: np.random.Generator, name: str, R: int = 50, T: int = 3000, burn: int = BURN_IN):
+    """Coupled AR(1) pair of Eq. 12 / Eq. 13 with the Table 1 parameters of scenario `name`:
+    x(t) = a_X x(t-1) + gamma_YX(t) y(t - d_YX) + eta_X,  y(t) = a_Y y(t-1) + gamma_XY(t) x(t - d_XY) + eta_Y,
+    unit-variance Gaussian noise; returns (src = x, tgt = y)."""
+    p = AR1_SCENARIOS[name]
+    L = T + burn
+    ex = rng.standard_normal((R, L))
+    ey = rng.standard_normal((R, L))
+    gxy, gyx = ar1_couplings(name, np.arange(L, dtype=np.float64) - burn)
+    x = np.zeros((R, L))
+    y = np.zeros((R, L))
+    for t in range(L):
+        xt = ex[:, t].copy()
+        yt = ey[:, t].copy()
+        if t >= 1:
+            xt += p["ax"] * x[:, t - 1]
+            yt += p["ay"] * y[:, t - 1]
+        if p["byx"] != 0.0 and t >= p["dyx"]:
+            xt += gyx[t] * y[:, t - p["dyx"]]
+        if t >= p["dxy"]:
+            yt += gxy[t] * x[:, t - p["dxy"]]
+        x[:, t] = xt
+        y[:, t] = yt
+    return (np.ascontiguousarray(x[:, burn:], dtype=np.float32),
+            np.ascontiguousarray(y[:, burn:], dtype=np.float32))
+
+
 def permutations(rng: np.random.Generator, S: int, R: int) -> np.ndarray:
     """S uniform random permutations of 0..R-1 (surrogate trial pairings), int32 [S][R]."""
     out = np.empty((S, R), dtype=np.int32)
@@ -274,6 +322,24 @@ def config(cid: int, *, n_t: Optional[int] = None, S: Optional[int] = None,
         return Workload("C5 large ensemble, 12000 points x 11-D, 200 t x (1+200)", [s],
                         _surrogate_instances([ts], 3, SS), k=4, t_starts=[ts], window=3, S=SS)
     raise ValueError(f"unknown config {cid}")
+
+
+def ar1_analysis(name: str = "unidirectional", S: int = 500, R: int = 50, window: int = 300,
+                 n_windows: int = None, seed: int = 0) -> Workload:
+    """The paper's AR(1) analysis: 50 trials x 3000 samples, d = 1, tau = 1, analysis windows of
+    300 samples from sample 200 on (4 windows for the unidirectional scenario, 8 otherwise),
+    delays scanned over 1..20 (1..30 for the bidirectional scenario), S surrogates, k = 4.
+    The instances hold the original and surrogates at the true delay; a delay scan supplies u."""
+    rng = np.random.default_rng(BASE_SEED + 60 + seed + list(AR1_SCENARIOS).index(name))
+    src, tgt = ar1_scenario(rng, name, R=R)
+    perms = permutations(rng, S, R)
+    s = Series(src, tgt, d=1, tau=1, u=AR1_SCENARIOS[name]["dxy"], perms=perms)
+    nw = n_windows or (4 if name == "unidirectional" else 8)
+    ts = [200 + window * j for j in range(nw)]
+    u_hi = 30 if name == "bidirectional" else 20
+    return Workload(f"AR(1) {name} scenario (Table 1), {R} trials, windows of {window}", [s],
+                    _surrogate_instances([ts], window, S), k=4, t_starts=[ts], window=window, S=S,
+                    extra=dict(u_lo=1, u_hi=u_hi))
 
 
 def sample_instances(w: Workload, n: int, seed: int = 0) -> List[int]:

@@ -28,7 +28,7 @@ _STATUS = {0: "TE_OK", 1: "TE_EINVAL", 2: "TE_ERANGE", 3: "TE_ENOMEM", 4: "TE_EC
 EXPORTS = ["te_create", "te_destroy", "te_last_error", "te_sync_status", "te_embed",
            "te_knn_maxnorm", "te_range_count", "te_estimate", "te_surrogate_test",
            "te_set_profiling", "te_last_kernel_ms", "te_last_launch_count", "te_set_launch_config",
-           "te_set_batching", "te_surrogate_test_static", "te_autotune"]
+           "te_set_batching", "te_surrogate_test_static", "te_autotune", "te_delay_scan"]
 
 
 class TEError(RuntimeError):
@@ -89,11 +89,12 @@ def load() -> C.CDLL:
     lib.te_last_launch_count.argtypes = [P]
     lib.te_set_launch_config.argtypes = [P, i32, i32]
     lib.te_set_batching.argtypes = [P, i32]
+    lib.te_delay_scan.argtypes = [P, C.POINTER(te_series), P, i32, i32, i32, i32, i32, i32, P, P, P, P]
     lib.te_autotune.argtypes = [P, C.POINTER(te_series), i32, C.POINTER(te_instance), i32, i32,
                                 C.c_char_p, C.POINTER(i32), C.POINTER(i32), P]
     for name in ("te_sync_status", "te_embed", "te_knn_maxnorm", "te_range_count", "te_estimate",
                  "te_surrogate_test", "te_set_profiling", "te_last_kernel_ms",
-                 "te_last_launch_count", "te_set_launch_config", "te_set_batching", "te_autotune"):
+                 "te_last_launch_count", "te_set_launch_config", "te_set_batching", "te_autotune", "te_delay_scan"):
         getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -327,3 +328,20 @@ def te_autotune(h: Handle, series: Sequence[DeviceSeries], instances: Sequence, 
                               None if cache_path is None else cache_path.encode(),
                               C.byref(t), C.byref(q), _stream(stream)))
     return int(t.value), int(q.value)
+
+
+def te_delay_scan(h: Handle, series: DeviceSeries, t_starts: Sequence[int], window: int, u_lo: int,
+                  u_hi: int, S: int, k: int, out=None, stream=None):
+    """TE for every scanned delay u_lo..u_hi and start, p-values, and the argmax delay per start."""
+    dev = series.src.device
+    n_u, n_t = u_hi - u_lo + 1, len(t_starts)
+    ser = _series_array([series])
+    ts = (C.c_int32 * max(1, n_t))(*[int(t) for t in t_starts])
+    if out is None:
+        out = {"te": torch.empty((n_u, n_t), dtype=torch.float64, device=dev),
+               "p": torch.empty((n_u, n_t), dtype=torch.float64, device=dev),
+               "u_best": torch.empty(n_t, dtype=torch.int32, device=dev)}
+    h.check(h.lib.te_delay_scan(h.h, ser, C.cast(ts, C.c_void_p), n_t, int(window), int(u_lo), int(u_hi),
+                                int(S), int(k), _ptr(out["te"]), _ptr(out["p"]), _ptr(out["u_best"]),
+                                _stream(stream)))
+    return out
