@@ -242,7 +242,10 @@ def bench_ours(args):
         return te.te_estimate(h, series_dev, w.instances, w.k, te=outs)
 
     tuned = None
-    if not args.no_autotune:
+    if args.shape:
+        tuned = tuple(int(v) for v in args.shape.lower().split("x"))
+        te.te_set_launch_config(h, tuned[0], tuned[1])
+    elif not args.no_autotune:
         tuned = te.te_autotune(h, ds, w.instances, w.k)
     outs = None
     if scan:
@@ -432,7 +435,7 @@ def bench_ours(args):
                    "l2": "256 MiB buffer written between timed steps (inputs smaller than L2)",
                    "per_rank": "every rank runs the full workload (weak scaling)",
                    "launch_shape": None if tuned is None else {"threads": tuned[0], "queries_per_thread": tuned[1],
-                                                               "chosen_by": "te_autotune"}},
+                                                               "chosen_by": "--shape" if args.shape else "te_autotune"}},
         "te_estimates_per_s": te_rate,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks, "per_launch": per,
@@ -492,6 +495,7 @@ def main():
     ap.add_argument("--per-launch-instances", type=int, default=2002)
     ap.add_argument("--no-per-launch", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--shape", default=None, help="fixed launch shape THREADSxQPT instead of autotuning")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-instances", type=int, default=32)
