@@ -337,10 +337,10 @@ def te_delay_scan(h: Handle, series: DeviceSeries, t_starts: Sequence[int], wind
     n_u, n_t = u_hi - u_lo + 1, len(t_starts)
     ser = _series_array([series])
     ts = (C.c_int32 * max(1, n_t))(*[int(t) for t in t_starts])
-    if out is None:
-        out = {"te": torch.empty((n_u, n_t), dtype=torch.float64, device=dev),
-               "p": torch.empty((n_u, n_t), dtype=torch.float64, device=dev),
-               "u_best": torch.empty(n_t, dtype=torch.int32, device=dev)}
+    if out is None:  # sizes clamped to >= 1 so that the library, not torch, rejects bad ranges
+        out = {"te": torch.empty((max(n_u, 1), max(n_t, 1)), dtype=torch.float64, device=dev),
+               "p": torch.empty((max(n_u, 1), max(n_t, 1)), dtype=torch.float64, device=dev),
+               "u_best": torch.empty(max(n_t, 1), dtype=torch.int32, device=dev)}
     h.check(h.lib.te_delay_scan(h.h, ser, C.cast(ts, C.c_void_p), n_t, int(window), int(u_lo), int(u_hi),
                                 int(S), int(k), _ptr(out["te"]), _ptr(out["p"]), _ptr(out["u_best"]),
                                 _stream(stream)))
