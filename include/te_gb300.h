@@ -200,6 +200,22 @@ te_status te_autotune(te_handle* h, const te_series* series, int32_t n_series, c
                       int32_t n_inst, int32_t k, const char* cache_path, int32_t* threads_out,
                       int32_t* qpt_out, void* stream);
 
+/* Search mode of te_estimate / te_surrogate_test / te_delay_scan (results are identical):
+ *   1 (default): sorted sweep. The points of every (series, window start, window) group are sorted
+ *      by the target coordinate y_{t'-1} (shared by the original and all surrogates of the group)
+ *      and each warp visits only references whose key lies inside the window its queries' radii
+ *      allow: every distance the estimator compares is at least fl(|key_q - key_j|), and the window
+ *      bounds are rounded outward, so no reference that could enter a top-k list or a count is
+ *      skipped. Used when every point count is <= 16384 (otherwise the exhaustive search runs).
+ *   0: exhaustive search over all N^2 pairs (the paper's brute force, Implementation section). */
+te_status te_set_search(te_handle* h, int32_t mode);
+
+/* Work of the last te_estimate / te_surrogate_test / te_delay_scan call: (query, reference)
+ * pair evaluations over both passes and the FP32 operations they cost (2 D per pair), counted on
+ * the device by the sweep (synchronises the device) or N^2 per pass for the exhaustive search;
+ * `swept` (nullable) is 1 when the sweep ran. */
+te_status te_last_work(te_handle* h, uint64_t* pairs, uint64_t* ops, int32_t* swept);
+
 /* Batching mode of te_estimate / te_surrogate_test. per_instance = 0 (default): one persistent
  * launch for the whole batch, captured in a CUDA graph. per_instance = 1: the same kernel and
  * tables, launched once per instance with a grid of that instance's work items and no graph,

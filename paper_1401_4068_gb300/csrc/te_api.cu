@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -28,6 +29,7 @@ constexpr int kMaxD = 32;             // te_knn_maxnorm / te_range_count
 constexpr int kMaxEmbedDim = 15;      // te_embed: D = 1 + 2d <= 31
 constexpr int kMaxBatchedD = 5;       // te_estimate / te_surrogate_test
 constexpr int kSmemCapBytes = 64 * 1024;  // reference tile budget of the batched kernel
+constexpr int kSweepSmemMaxBytes = 160 * 1024;  // sweep mode: room for whole query blocks per tile
 
 std::string g_create_error;
 
@@ -99,6 +101,11 @@ struct HostBuf {  // pinned staging for asynchronous uploads
 struct Plan {
     std::vector<InstDesc> insts;  // caller order
     std::vector<WorkItem> items;  // cost order, items of an instance contiguous
+    std::vector<te::SortGroup> groups;  // sweep mode: one sorted order per (series, start, window)
+    int64_t sorted_total = 0;
+    int nmax = 0;
+    uint64_t exhaustive_pairs = 0;  // pair evaluations of the exhaustive search (both passes)
+    uint64_t exhaustive_ops = 0;
     BatchedVariant var{};
     int threads = 0, grid = 0, smem_floats = 0;
     size_t smem = 0;
@@ -138,12 +145,19 @@ struct te_handle {
     int cfg_threads = 0, cfg_qpt = 0;
     std::map<std::string, std::pair<int, int>> tuned;  // batch signature -> (threads, qpt)
     bool per_instance = false;  // one launch per instance instead of one persistent launch
+    int search_mode = 1;        // 1: sorted sweep where it applies, 0: exhaustive search
+    bool last_sweep = false;
+    uint64_t last_pairs = 0, last_ops = 0;
 
     DevBuf<InstDesc> d_insts;
     DevBuf<WorkItem> d_items;
     DevBuf<int32_t> d_words;  // [0] queue head, [1] flags
     DevBuf<double> d_partial, d_partial_abs, d_te_all, d_surr_ws, d_p_ws;
     DevBuf<float2> d_psi;
+    DevBuf<te::SortGroup> d_groups;
+    DevBuf<int32_t> d_sidx;
+    DevBuf<float> d_skey;
+    DevBuf<unsigned long long> d_exec;
     HostBuf<unsigned char> h_stage;
     int workspace_gen = 0;
 
@@ -246,7 +260,8 @@ std::string shape_signature(const std::vector<InstDesc>& insts, int ks) {
 void choose_shape(te_handle* h, const std::vector<InstDesc>& insts, int ks, int* threads, int* qpt) {
     int dmax = 1;
     for (const auto& I : insts) dmax = std::max(dmax, I.d);
-    int q = (ks == 5 && dmax <= 4) ? 4 : 2;
+    // the sweep prefers 2 (narrower key windows per warp, no register spills)
+    int q = (ks == 5 && dmax <= 4 && h->search_mode == 0) ? 4 : 2;
     if (h->cfg_qpt) q = ks == 5 ? h->cfg_qpt : 2;
     *qpt = q;
     if (h->cfg_threads) {
@@ -346,7 +361,39 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
     }
     P->smem_floats = std::min(kSmemCapBytes / 4, dmaxN);
     P->smem_floats = std::max(P->smem_floats, 4 * 11);
+    P->nmax = nmax;
+    // sweep mode: every instance must either fit one tile or leave room for a whole CTA query
+    // block per tile (its queries then lie in one tile)
+    bool sweep = h->search_mode == 1 && nmax <= te::kSweepMaxN;
+    if (sweep) {
+        int need = P->smem_floats;
+        for (const auto& I : P->insts) {
+            const int D = 1 + 2 * I.d;
+            if ((int64_t)((I.N + 3) & ~3) * D > P->smem_floats) need = std::max(need, per * D);
+        }
+        if (need * (int)sizeof(float) > kSweepSmemMaxBytes) sweep = false;
+        else P->smem_floats = need;
+    }
+    P->var.sweep = sweep;
     P->smem = (size_t)P->smem_floats * sizeof(float);
+    for (const auto& I : P->insts) {
+        P->exhaustive_pairs += 2ull * (uint64_t)I.N * (uint64_t)I.N;
+        P->exhaustive_ops += 2ull * (uint64_t)I.N * (uint64_t)I.N * 2ull * (uint64_t)(1 + 2 * I.d);
+    }
+    if (sweep) {
+        std::map<std::tuple<const float*, int, int, int, int>, int64_t> gidx;
+        for (auto& I : P->insts) {
+            auto key = std::make_tuple(I.tgt, I.T, I.R, I.t_start, I.W);
+            auto f = gidx.find(key);
+            if (f == gidx.end()) {
+                te::SortGroup G{I.tgt, I.R, I.T, I.W, I.t_start, I.N, 0, P->sorted_total};
+                P->groups.push_back(G);
+                f = gidx.emplace(key, P->sorted_total).first;
+                P->sorted_total += I.N;
+            }
+            I.sort_off = f->second;
+        }
+    }
     // bound on the summation error relative to sum |terms| (see te_estimate in the header):
     // 3*qpt float-float additions per thread (<= 2^-46 each), table rounding (2^-47), FP64
     // reductions over threads and items
@@ -367,16 +414,41 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
 // Upload the plan's tables (pinned staging -> device on `stream`).
 te_status upload_tables(te_handle* h, const Plan& P, cudaStream_t stream) {
     const size_t bi = P.insts.size() * sizeof(InstDesc), bt = P.items.size() * sizeof(WorkItem);
+    const size_t bg = P.groups.size() * sizeof(te::SortGroup);
     cudaError_t e;
     if ((e = cudaEventSynchronize(h->upload_done)) != cudaSuccess) return h->cuda_fail(e, "staging reuse");
-    if ((e = h->h_stage.ensure(bi + bt)) != cudaSuccess) return h->fail(TE_ENOMEM, "pinned staging");
+    if ((e = h->h_stage.ensure(bi + bt + bg)) != cudaSuccess) return h->fail(TE_ENOMEM, "pinned staging");
     std::memcpy(h->h_stage.p, P.insts.data(), bi);
     std::memcpy(h->h_stage.p + bi, P.items.data(), bt);
+    if (bg) std::memcpy(h->h_stage.p + bi + bt, P.groups.data(), bg);
     if ((e = cudaMemcpyAsync(h->d_insts.p, h->h_stage.p, bi, cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
         (e = cudaMemcpyAsync(h->d_items.p, h->h_stage.p + bi, bt, cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
+        (bg && (e = cudaMemcpyAsync(h->d_groups.p, h->h_stage.p + bi + bt, bg, cudaMemcpyHostToDevice, stream)) !=
+                   cudaSuccess) ||
         (e = cudaEventRecord(h->upload_done, stream)) != cudaSuccess)
         return h->cuda_fail(e, "table upload");
     return TE_OK;
+}
+
+// sweep mode: workspace for the sorted orders and the work counters, the sort kernel's limit
+te_status prepare_sweep(te_handle* h, const Plan& P, bool* grew) {
+    if (!P.var.sweep) return TE_OK;
+    cudaError_t e;
+    if ((e = h->d_groups.ensure(P.groups.size(), grew)) != cudaSuccess ||
+        (e = h->d_sidx.ensure((size_t)P.sorted_total, grew)) != cudaSuccess ||
+        (e = h->d_skey.ensure((size_t)P.sorted_total, grew)) != cudaSuccess ||
+        (e = h->d_exec.ensure(2, grew)) != cudaSuccess)
+        return h->fail(TE_ENOMEM, "sweep workspace: %s", cudaGetErrorString(e));
+    if ((e = te::prepare_sort_kernel(P.nmax)) != cudaSuccess) return h->cuda_fail(e, "sort kernel attribute");
+    return TE_OK;
+}
+
+// the sweep's pre-pass (work counters cleared, groups sorted) on `s`
+cudaError_t launch_sweep_prepass(te_handle* h, const Plan& P, cudaStream_t s) {
+    if (!P.var.sweep) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(h->d_exec.p, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    return te::launch_sort_groups(h->d_groups.p, (int)P.groups.size(), P.nmax, h->d_sidx.p, h->d_skey.p, s);
 }
 
 BatchArgs batch_args(te_handle* h, const Plan& P, int k, int32_t* counts, float* eps) {
@@ -393,6 +465,11 @@ BatchArgs batch_args(te_handle* h, const Plan& P, int k, int32_t* counts, float*
     a.partial_abs = h->d_partial_abs.p;
     a.counts_out = counts;
     a.eps_out = eps;
+    if (P.var.sweep) {
+        a.sorted_idx = h->d_sidx.p;
+        a.sorted_key = h->d_skey.p;
+        a.exec = h->d_exec.p;
+    }
     return a;
 }
 
@@ -408,6 +485,10 @@ te_status run_per_instance(te_handle* h, const Plan& P, int n_inst, int k, doubl
     if (e != cudaSuccess) return h->cuda_fail(e, "clear queues");
     const BatchArgs a = batch_args(h, P, k, counts, eps);
     int launches = 0;
+    if (P.var.sweep) {
+        if ((e = launch_sweep_prepass(h, P, stream)) != cudaSuccess) return h->cuda_fail(e, "sort pre-pass");
+        ++launches;
+    }
     for (int i = 0; i < n_inst; ++i) {
         const InstDesc& I = P.insts[i];
         BatchArgs ai = a;
@@ -455,6 +536,10 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
         (e = h->d_partial_abs.ensure(P.items.size(), &grew)) != cudaSuccess ||
         (n_groups > 0 && (e = h->d_te_all.ensure((size_t)n_inst, &grew)) != cudaSuccess))
         return h->fail(TE_ENOMEM, "workspace: %s", cudaGetErrorString(e));
+    if ((st = prepare_sweep(h, P, &grew)) != TE_OK) return st;
+    h->last_sweep = P.var.sweep;
+    h->last_pairs = P.exhaustive_pairs;
+    h->last_ops = P.exhaustive_ops;
     if (grew) {
         ++h->workspace_gen;
         // a fresh flag word must start cleared
@@ -470,7 +555,7 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
     const void* outs[] = {te_out, err, counts, eps, te_orig, te_surr, p};
     key = fnv(key, outs, sizeof outs);
     const int cfg[] = {k, P.threads, P.grid, P.smem_floats, P.var.dlo, P.var.dhi, P.var.ks, P.var.qpt,
-                       n_groups, S, h->profiling ? 1 : 0, n_inst};
+                       n_groups, S, h->profiling ? 1 : 0, n_inst, P.var.sweep ? 1 : 0};
     key = fnv(key, cfg, sizeof cfg);
     const bool replay = !h->per_instance && h->graph_exec && h->graph_key == key &&
                         h->graph_gen == h->workspace_gen;
@@ -489,6 +574,10 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
             return h->cuda_fail(e, "begin capture");
         cudaError_t ce = cudaMemsetAsync(h->d_words.p, 0, sizeof(int32_t), h->cap_stream);
         int launches = 0;
+        if (ce == cudaSuccess && P.var.sweep) {
+            ce = launch_sweep_prepass(h, P, h->cap_stream);
+            ++launches;
+        }
         // an event recorded during capture becomes a graph node only with cudaEventRecordExternal
         if (ce == cudaSuccess && h->profiling) ce = cudaEventRecordWithFlags(h->ev0, h->cap_stream, cudaEventRecordExternal);
         if (ce == cudaSuccess) {
@@ -586,6 +675,10 @@ TE_EXPORT void te_destroy(te_handle* h) {
     h->d_surr_ws.release();
     h->d_p_ws.release();
     h->d_psi.release();
+    h->d_groups.release();
+    h->d_sidx.release();
+    h->d_skey.release();
+    h->d_exec.release();
     h->h_stage.release();
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
@@ -941,6 +1034,31 @@ TE_EXPORT te_status te_last_kernel_ms(te_handle* h, float* ms) {
 }
 
 TE_EXPORT int32_t te_last_launch_count(const te_handle* h) { return h ? h->last_launches : 0; }
+
+TE_EXPORT te_status te_set_search(te_handle* h, int32_t mode) {
+    if (!h) return TE_EINVAL;
+    if (mode != 0 && mode != 1) return h->fail(TE_EINVAL, "te_set_search: mode %d is not 0 or 1", mode);
+    h->search_mode = mode;
+    return TE_OK;
+}
+
+TE_EXPORT te_status te_last_work(te_handle* h, uint64_t* pairs, uint64_t* ops, int32_t* swept) {
+    if (!h) return TE_EINVAL;
+    h->err.clear();
+    uint64_t pr = h->last_pairs, op = h->last_ops;
+    if (h->last_sweep && h->d_exec.p) {
+        DeviceGuard g(h->device);
+        unsigned long long v[2] = {0, 0};
+        cudaError_t e = cudaMemcpy(v, h->d_exec.p, sizeof v, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return h->cuda_fail(e, "read work counters");
+        pr = v[0];
+        op = v[1];
+    }
+    if (pairs) *pairs = pr;
+    if (ops) *ops = op;
+    if (swept) *swept = h->last_sweep ? 1 : 0;
+    return TE_OK;
+}
 
 TE_EXPORT te_status te_set_batching(te_handle* h, int32_t per_instance) {
     if (!h) return TE_EINVAL;

@@ -132,52 +132,4 @@ __device__ __forceinline__ void process_item(const BatchArgs& a, const InstDesc&
     }
 }
 
-template <int DLO, int DHI, int Q, int KS>
-__global__ void __launch_bounds__(kBatchedMaxThreads) batched_kernel(const BatchArgs a) {
-    extern __shared__ __align__(16) float sm[];
-    __shared__ double sred[64];
-    __shared__ int s_item;
-    for (;;) {
-        __syncthreads();  // everyone is done with s_item / sred of the previous item
-        if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
-        __syncthreads();
-        const int it = s_item;
-        if (it >= a.n_items) break;
-        const WorkItem w = a.items[it];
-        const InstDesc I = a.insts[w.inst];
-        if constexpr (DLO == DHI) {
-            process_item<DLO, Q, KS>(a, I, w.q0, it, sm, sred);
-        } else {
-            switch (I.d) {
-                case 1: if constexpr (DLO <= 1 && 1 <= DHI) process_item<1, Q, KS>(a, I, w.q0, it, sm, sred); break;
-                case 2: if constexpr (DLO <= 2 && 2 <= DHI) process_item<2, Q, KS>(a, I, w.q0, it, sm, sred); break;
-                case 3: if constexpr (DLO <= 3 && 3 <= DHI) process_item<3, Q, KS>(a, I, w.q0, it, sm, sred); break;
-                case 4: if constexpr (DLO <= 4 && 4 <= DHI) process_item<4, Q, KS>(a, I, w.q0, it, sm, sred); break;
-                case 5: if constexpr (DLO <= 5 && 5 <= DHI) process_item<5, Q, KS>(a, I, w.q0, it, sm, sred); break;
-                default: break;
-            }
-        }
-    }
-}
-
-// kernel pointer of one variant (defined in te_batched_*.cu); k > 4 runs with 2 queries per
-// thread only (17 slots x 4 queries would not fit the register budget)
-#define TE_BATCHED_PTR_FN(NAME, DLO, DHI)                                            \
-    const void* NAME(int ks, int q) {                                                \
-        if (q == 2) {                                                                \
-            if (ks == 5) return (const void*)batched_kernel<DLO, DHI, 2, 5>;         \
-            if (ks == 17) return (const void*)batched_kernel<DLO, DHI, 2, 17>;       \
-        } else if (q == 4) {                                                         \
-            if (ks == 5) return (const void*)batched_kernel<DLO, DHI, 4, 5>;         \
-        }                                                                            \
-        return nullptr;                                                              \
-    }
-
-const void* batched_ptr_d1(int ks, int q);
-const void* batched_ptr_d2(int ks, int q);
-const void* batched_ptr_d3(int ks, int q);
-const void* batched_ptr_d4(int ks, int q);
-const void* batched_ptr_d5(int ks, int q);
-const void* batched_ptr_mix(int ks, int q);
-
 }  // namespace te

@@ -79,15 +79,15 @@ cudaError_t launch_delay_argmax(const double* te, int n_u, int n_t, int u_lo, in
 const void* batched_kernel_ptr(const BatchedVariant& v) {
     if (v.dlo == v.dhi) {
         switch (v.dlo) {
-            case 1: return batched_ptr_d1(v.ks, v.qpt);
-            case 2: return batched_ptr_d2(v.ks, v.qpt);
-            case 3: return batched_ptr_d3(v.ks, v.qpt);
-            case 4: return batched_ptr_d4(v.ks, v.qpt);
-            case 5: return batched_ptr_d5(v.ks, v.qpt);
+            case 1: return batched_ptr_d1(v.ks, v.qpt, v.sweep);
+            case 2: return batched_ptr_d2(v.ks, v.qpt, v.sweep);
+            case 3: return batched_ptr_d3(v.ks, v.qpt, v.sweep);
+            case 4: return batched_ptr_d4(v.ks, v.qpt, v.sweep);
+            case 5: return batched_ptr_d5(v.ks, v.qpt, v.sweep);
             default: return nullptr;
         }
     }
-    return batched_ptr_mix(v.ks, v.qpt);
+    return batched_ptr_mix(v.ks, v.qpt, v.sweep);
 }
 
 cudaError_t launch_batched(const BatchedVariant& v, const BatchArgs& a, int grid, int threads,

@@ -17,9 +17,22 @@ struct InstDesc {
     int32_t R, T, W, t_start;
     int32_t tau, u, d, N;  // N = R * W points, joint dimension 1 + 2d
     int64_t pt_off;        // offset of this instance's points in concatenated eps/counts outputs
+    int64_t sort_off;      // offset of its group's sorted order in the sweep arrays (sweep mode)
     int32_t item_begin;    // its work items are item_begin .. item_begin + n_items - 1
     int32_t n_items;
 };
+
+// Points of one (series, window start, window) group: the estimates of a group (original and
+// surrogates) share the target coordinates, so they share one order of the points sorted by the
+// target coordinate y_{t'-1} (coordinate 1 of the joint space).
+struct SortGroup {
+    const float* tgt;
+    int32_t R, T, W, t_start, N, pad;
+    int64_t off;           // offset of the group's sorted index / key arrays
+};
+
+// Largest point count the sweep mode sorts (in shared memory, one CTA per group).
+constexpr int kSweepMaxN = 16384;
 
 // One unit of work of the persistent kernel: queries q0 .. q0 + threads*qpt - 1 of an instance.
 struct WorkItem {
@@ -46,6 +59,9 @@ struct BatchArgs {
     double* partial_abs;     // [n_items] per-item sum of |terms| (for the error bound)
     int32_t* counts_out;     // nullable: per instance [3][N] at 3 * pt_off
     float* eps_out;          // nullable: per instance [N] at pt_off
+    const int32_t* sorted_idx;  // sweep mode: per group, point indices in ascending key order
+    const float* sorted_key;    // sweep mode: the keys in that order
+    unsigned long long* exec;   // sweep mode: [0] evaluated (query, reference) pairs, [1] FP32 ops
 };
 
 // ---- launchers (te_unit.cu) ----
@@ -61,8 +77,18 @@ cudaError_t launch_count(const float* pts, int N, int dy, int dx, int ld, const 
 // Variant of the persistent kernel: d in [dlo, dhi] (dlo == dhi: specialised), ks = k-slots.
 struct BatchedVariant {
     int dlo, dhi, ks, qpt;
+    bool sweep;  // sorted-sweep search instead of the exhaustive one
 };
+cudaError_t launch_sort_groups(const SortGroup* groups, int n_groups, int nmax, int32_t* idx, float* key,
+                               cudaStream_t s);
+cudaError_t prepare_sort_kernel(int nmax);
 const void* batched_kernel_ptr(const BatchedVariant& v);
+const void* batched_ptr_d1(int ks, int q, bool sweep);
+const void* batched_ptr_d2(int ks, int q, bool sweep);
+const void* batched_ptr_d3(int ks, int q, bool sweep);
+const void* batched_ptr_d4(int ks, int q, bool sweep);
+const void* batched_ptr_d5(int ks, int q, bool sweep);
+const void* batched_ptr_mix(int ks, int q, bool sweep);
 cudaError_t launch_batched(const BatchedVariant& v, const BatchArgs& a, int grid, int threads,
                            size_t smem, cudaStream_t s);
 cudaError_t launch_finalize_te(const InstDesc* insts, int n_inst, const double* partial,

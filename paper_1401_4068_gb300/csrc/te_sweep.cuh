@@ -1,0 +1,345 @@
+// Sweep mode of the batched kernel: the same exact estimator as process_item (Eq. 9 / Eq. 10),
+// with the reference points of an instance visited in the order of their target coordinate
+// y_{t'-1} (coordinate 1, a coordinate of the y- group) so that references that cannot matter
+// are never evaluated.
+//
+// Why it is exact: for a query q with current radius r (its (k+1)-th smallest distance so far in
+// pass 1, its final eps in pass 2) and a reference j, every distance the estimator uses to decide
+// (the joint distance of pass 1, b = max over y- of pass 2, and hence max(a, b) and max(b, x))
+// is at least fl(|key_q - key_j|). With bounds rounded outward,
+//   key_j <= fsub_rd(key_q, r)  or  key_j >= fadd_ru(key_q, r)   =>   fl(|key_q - key_j|) >= r,
+// so such a reference can neither enter the top-k list (strict < r) nor be counted (strict < eps).
+// Queries of a warp are a contiguous block of the sorted order; a warp first evaluates its own
+// block (tight radii early), then sweeps right and left and stops on each side at the first
+// group of four references entirely outside its window. Radii only shrink during pass 1, so a
+// window computed earlier is a superset of the current one.
+#pragma once
+
+#include "te_batched.cuh"
+
+namespace te {
+
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// CTA-wide min of a and max of b (every thread gets both); sb: 64 floats of shared memory
+__device__ __forceinline__ void block_minmax(float& a, float& b, float* sb) {
+    a = warp_min(a);
+    b = warp_max(b);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        sb[warp] = a;
+        sb[32 + warp] = b;
+    }
+    __syncthreads();
+    a = sb[0];
+    b = sb[32];
+    for (int w = 1; w < nw; ++w) {
+        a = fminf(a, sb[w]);
+        b = fmaxf(b, sb[32 + w]);
+    }
+}
+
+template <int d>
+__device__ __forceinline__ void stage_tile_sorted(const InstDesc& I, const int32_t* __restrict__ sidx, int base,
+                                                  int nv, int ldt, float* sm, int32_t* flags) {
+    constexpr int D = 1 + 2 * d;
+    const int nfill = (nv + 3) & ~3;
+    for (int p = threadIdx.x; p < nfill; p += blockDim.x) {
+        float v[D];
+        if (p < nv) {
+            gather_point<d>(I, __ldg(sidx + base + p), v, flags);
+        } else {
+#pragma unroll
+            for (int c = 0; c < D; ++c) v[c] = f_inf();
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) sm[c * ldt + p] = v[c];
+    }
+}
+
+// window of the warp around its queries' keys for radii r (outward rounded, invalid slots ignored)
+template <int Q>
+__device__ __forceinline__ void warp_window(const float (&qkey)[Q], const bool (&qv)[Q], const float (&r)[Q],
+                                            float& lb, float& rb) {
+    lb = f_inf();
+    rb = -f_inf();
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+        if (qv[q]) {
+            lb = fminf(lb, __fsub_rd(qkey[q], r[q]));
+            rb = fmaxf(rb, __fadd_ru(qkey[q], r[q]));
+        }
+    lb = warp_min(lb);
+    rb = warp_max(rb);
+}
+
+template <int Q, int KS>
+__device__ __forceinline__ void current_radii(const float (&t)[Q][KS], float (&r)[Q]) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) r[q] = t[q][KS - 1];
+}
+
+// one group of four references (group j of the staged tile) against the warp's queries, pass 1
+template <int D, int Q, int KS>
+__device__ __forceinline__ void knn_group(const float* __restrict__ s, int ldt, int j, const u64 (&qq)[Q][D],
+                                          float (&t)[Q][KS]) {
+    ulonglong2 r[D];
+    load_refs4<D>(s, ldt, j, r);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        float dx[D], dy[D], dz[D], dw[D];
+        diff4<D>(qq[q], r, dx, dy, dz, dw);
+        topk_push(t[q], absmax_range<0, D - 1>(dx));
+        topk_push(t[q], absmax_range<0, D - 1>(dy));
+        topk_push(t[q], absmax_range<0, D - 1>(dz));
+        topk_push(t[q], absmax_range<0, D - 1>(dw));
+    }
+}
+
+// pass 1 over groups [g0, g1) of the staged tile: dir 0 evaluates all of them (the warp's own
+// block), dir +1 ascends and stops at the first group whose smallest key is right of the
+// window, dir -1 descends and stops at the first group whose largest key is left of it.
+// Returns the number of groups evaluated; sets `done` when it stopped at a window edge.
+template <int D, int Q, int KS>
+__device__ __forceinline__ int knn_range(const float* __restrict__ s, int ldt, int g0, int g1, int dir,
+                                         const u64 (&qq)[Q][D], const float (&qkey)[Q], const bool (&qv)[Q],
+                                         float (&t)[Q][KS], bool& done) {
+    float r[Q], lb, rb;
+    current_radii(t, r);
+    warp_window(qkey, qv, r, lb, rb);
+    int n = 0;
+#pragma unroll 1
+    for (int jj = g0; jj < g1; ++jj) {
+        const int j = dir < 0 ? g1 - 1 - (jj - g0) : jj;
+        if (dir > 0 && s[ldt + 4 * j] >= rb) {
+            done = true;
+            break;
+        }
+        if (dir < 0 && s[ldt + 4 * j + 3] <= lb) {
+            done = true;
+            break;
+        }
+        knn_group<D, Q, KS>(s, ldt, j, qq, t);
+        if ((++n & 3) == 0 && dir != 0) {
+            current_radii(t, r);
+            warp_window(qkey, qv, r, lb, rb);
+        }
+    }
+    return n;
+}
+
+// pass 2 over groups [g0, g1) ascending, skipping groups left of the window [lb, rb] and
+// stopping at the first group right of it
+template <int DY, int DX, int Q>
+__device__ __forceinline__ int count_range(const float* __restrict__ s, int ldt, int g0, int g1, float lb, float rb,
+                                           const u64 (&qq)[Q][1 + DY + DX], const float (&e)[Q], float (&cz)[Q],
+                                           float (&cyz)[Q], float (&cxz)[Q]) {
+    constexpr int D = 1 + DY + DX;
+    int n = 0;
+#pragma unroll 1
+    for (int j = g0; j < g1; ++j) {
+        if (s[ldt + 4 * j] >= rb) break;
+        if (s[ldt + 4 * j + 3] <= lb) continue;
+        ulonglong2 r[D];
+        load_refs4<D>(s, ldt, j, r);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            float dx[D], dy[D], dz[D], dw[D];
+            diff4<D>(qq[q], r, dx, dy, dz, dw);
+            count_one<DY, DX>(dx, e[q], cz[q], cyz[q], cxz[q]);
+            count_one<DY, DX>(dy, e[q], cz[q], cyz[q], cxz[q]);
+            count_one<DY, DX>(dz, e[q], cz[q], cyz[q], cxz[q]);
+            count_one<DY, DX>(dw, e[q], cz[q], cyz[q], cxz[q]);
+        }
+        ++n;
+    }
+    return n;
+}
+
+// first sorted position whose key is > x (keys ascending, n of them)
+__device__ __forceinline__ int first_greater(const float* __restrict__ key, int n, float x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(key + mid) > x) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+// first sorted position whose key is >= x
+__device__ __forceinline__ int first_not_less(const float* __restrict__ key, int n, float x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(key + mid) >= x) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+template <int d, int Q, int KS>
+__device__ __forceinline__ void process_item_sweep(const BatchArgs& a, const InstDesc& I, int q0, int it, float* sm,
+                                                   double* sred, float* sb) {
+    constexpr int D = 1 + 2 * d;
+    const int N = I.N;
+    const int T = blockDim.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int32_t* sidx = a.sorted_idx + I.sort_off;
+    const float* skey = a.sorted_key + I.sort_off;
+    // one tile when the instance fits, else tiles of whole CTA query blocks (a CTA's queries then
+    // lie in one tile)
+    const int block = T * Q;
+    int ldt = (N + 3) & ~3;
+    if (ldt * D > a.smem_floats) ldt = ((a.smem_floats / D) / block) * block;
+    const int ntile = (N + ldt - 1) / ldt;
+    const int ctile = q0 / ldt;
+
+    // queries: warp-contiguous runs of the sorted order
+    const int wbase = q0 + warp * 32 * Q;
+    u64 qq[Q][D];
+    float qkey[Q];
+    int qidx[Q];
+    bool qv[Q];
+    int nvalid = 0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int pos = wbase + q * 32 + lane;
+        qv[q] = pos < N;
+        float p[D];
+        if (qv[q]) {
+            qidx[q] = __ldg(sidx + pos);
+            gather_point<d>(I, qidx[q], p, a.flags);
+        } else {
+            qidx[q] = -1;
+#pragma unroll
+            for (int c = 0; c < D; ++c) p[c] = 0.0f;
+        }
+        qkey[q] = p[1];
+#pragma unroll
+        for (int c = 0; c < D; ++c) qq[q][c] = dup2(p[c]);
+        nvalid += __popc(__ballot_sync(0xffffffffu, qv[q]));
+    }
+    const bool warp_active = wbase < N;
+    unsigned long long groups_done = 0;
+
+    int staged = -1;
+    auto stage = [&](int ti) {
+        if (staged == ti) return;
+        const int base = ti * ldt;
+        __syncthreads();
+        stage_tile_sorted<d>(I, sidx, base, min(ldt, N - base), ldt, sm, a.flags);
+        __syncthreads();
+        staged = ti;
+    };
+    auto ngroups = [&](int ti) { return (min(ldt, N - ti * ldt) + 3) >> 2; };
+
+    // ---- pass 1: own block, then right, then left
+    float t[Q][KS];
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int m = 0; m < KS; ++m) t[q][m] = f_inf();
+    bool rdone = false, ldone = false;
+    stage(ctile);
+    if (warp_active) {
+        const int g_own0 = (wbase - ctile * ldt) >> 2;
+        const int g_own1 = min(ngroups(ctile), (min(wbase + 32 * Q, N) - ctile * ldt + 3) >> 2);
+        groups_done += knn_range<D, Q, KS>(sm, ldt, g_own0, g_own1, 0, qq, qkey, qv, t, rdone);
+        rdone = false;
+        groups_done += knn_range<D, Q, KS>(sm, ldt, g_own1, ngroups(ctile), +1, qq, qkey, qv, t, rdone);
+        groups_done += knn_range<D, Q, KS>(sm, ldt, 0, g_own0, -1, qq, qkey, qv, t, ldone);
+    }
+    for (int ti = ctile + 1; ti < ntile; ++ti) {  // right tiles
+        float r[Q], lb, rb;
+        current_radii(t, r);
+        warp_window(qkey, qv, r, lb, rb);
+        float blb = f_inf(), brb = (warp_active && !rdone) ? rb : -f_inf();
+        block_minmax(blb, brb, sb);
+        if (!(__ldg(skey + ti * ldt) < brb)) break;
+        stage(ti);
+        if (warp_active && !rdone)
+            groups_done += knn_range<D, Q, KS>(sm, ldt, 0, ngroups(ti), +1, qq, qkey, qv, t, rdone);
+    }
+    for (int ti = ctile - 1; ti >= 0; --ti) {  // left tiles
+        float r[Q], lb, rb;
+        current_radii(t, r);
+        warp_window(qkey, qv, r, lb, rb);
+        float blb = (warp_active && !ldone) ? lb : f_inf(), brb = -f_inf();
+        block_minmax(blb, brb, sb);
+        if (!(__ldg(skey + (ti + 1) * ldt - 1) > blb)) break;
+        stage(ti);
+        if (warp_active && !ldone)
+            groups_done += knn_range<D, Q, KS>(sm, ldt, 0, ngroups(ti), -1, qq, qkey, qv, t, ldone);
+    }
+    float e[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) e[q] = topk_select(t[q], a.k);
+
+    // ---- pass 2: only the key window (key_q - eps, key_q + eps) of the CTA's queries
+    float cz[Q], cyz[Q], cxz[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) cz[q] = cyz[q] = cxz[q] = 0.0f;
+    float lb, rb;
+    warp_window(qkey, qv, e, lb, rb);
+    float blb = warp_active ? lb : f_inf(), brb = warp_active ? rb : -f_inf();
+    block_minmax(blb, brb, sb);
+    const int plo = first_greater(skey, N, blb);
+    const int phi = first_not_less(skey, N, brb);
+    if (plo < phi) {
+        for (int ti = plo / ldt; ti <= (phi - 1) / ldt; ++ti) {
+            stage(ti);
+            if (warp_active)
+                groups_done += count_range<d, d, Q>(sm, ldt, 0, ngroups(ti), lb, rb, qq, e, cz, cyz, cxz);
+        }
+    }
+
+    // ---- digamma terms of Eq. 9 (compensated FP32 per thread), outputs at the original index
+    FF acc{0.0f, 0.0f};
+    float acc_abs = 0.0f;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        if (qv[q]) {
+            const int i = qidx[q];
+            const int self = e[q] > 0.0f ? 1 : 0;
+            const int nz = (int)cz[q] - self, nyz = (int)cyz[q] - self, nxz = (int)cxz[q] - self;
+            if (a.counts_out) {
+                int32_t* co = a.counts_out + 3 * I.pt_off;
+                co[i] = nz;
+                co[N + i] = nyz;
+                co[2 * N + i] = nxz;
+            }
+            if (a.eps_out) a.eps_out[I.pt_off + i] = e[q];
+            const float2 p1 = __ldg(a.psi + nz + 1);
+            const float2 p2 = __ldg(a.psi + nyz + 1);
+            const float2 p3 = __ldg(a.psi + nxz + 1);
+            acc = ff_add(acc, p1.x, p1.y);
+            acc = ff_add(acc, -p2.x, -p2.y);
+            acc = ff_add(acc, -p3.x, -p3.y);
+            acc_abs += fabsf(p1.x) + fabsf(p2.x) + fabsf(p3.x);
+        }
+    }
+    if (a.exec && warp_active && lane == 0) {
+        const unsigned long long pairs = groups_done * 4ull * (unsigned long long)nvalid;
+        atomicAdd(a.exec, pairs);
+        atomicAdd(a.exec + 1, pairs * 2ull * D);
+    }
+    double v = (double)acc.hi + (double)acc.lo;
+    double w = (double)acc_abs;
+    block_sum2(v, w, sred);
+    if (threadIdx.x == 0) {
+        a.partial[it] = v;
+        a.partial_abs[it] = w;
+    }
+}
+
+}  // namespace te

@@ -28,7 +28,8 @@ _STATUS = {0: "TE_OK", 1: "TE_EINVAL", 2: "TE_ERANGE", 3: "TE_ENOMEM", 4: "TE_EC
 EXPORTS = ["te_create", "te_destroy", "te_last_error", "te_sync_status", "te_embed",
            "te_knn_maxnorm", "te_range_count", "te_estimate", "te_surrogate_test",
            "te_set_profiling", "te_last_kernel_ms", "te_last_launch_count", "te_set_launch_config",
-           "te_set_batching", "te_surrogate_test_static", "te_autotune", "te_delay_scan"]
+           "te_set_batching", "te_surrogate_test_static", "te_autotune", "te_delay_scan",
+           "te_set_search", "te_last_work"]
 
 
 class TEError(RuntimeError):
@@ -89,12 +90,15 @@ def load() -> C.CDLL:
     lib.te_last_launch_count.argtypes = [P]
     lib.te_set_launch_config.argtypes = [P, i32, i32]
     lib.te_set_batching.argtypes = [P, i32]
+    lib.te_set_search.argtypes = [P, i32]
+    lib.te_last_work.argtypes = [P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(i32)]
     lib.te_delay_scan.argtypes = [P, C.POINTER(te_series), P, i32, i32, i32, i32, i32, i32, P, P, P, P]
     lib.te_autotune.argtypes = [P, C.POINTER(te_series), i32, C.POINTER(te_instance), i32, i32,
                                 C.c_char_p, C.POINTER(i32), C.POINTER(i32), P]
     for name in ("te_sync_status", "te_embed", "te_knn_maxnorm", "te_range_count", "te_estimate",
                  "te_surrogate_test", "te_set_profiling", "te_last_kernel_ms",
-                 "te_last_launch_count", "te_set_launch_config", "te_set_batching", "te_autotune", "te_delay_scan"):
+                 "te_last_launch_count", "te_set_launch_config", "te_set_batching", "te_autotune", "te_delay_scan",
+                 "te_set_search", "te_last_work"):
         getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -345,3 +349,15 @@ def te_delay_scan(h: Handle, series: DeviceSeries, t_starts: Sequence[int], wind
                                 int(S), int(k), _ptr(out["te"]), _ptr(out["p"]), _ptr(out["u_best"]),
                                 _stream(stream)))
     return out
+
+
+def te_set_search(h: Handle, sweep: bool):
+    """True: sorted sweep (default); False: exhaustive search over all pairs."""
+    h.check(h.lib.te_set_search(h.h, 1 if sweep else 0))
+
+
+def te_last_work(h: Handle):
+    """(pair evaluations, FP32 ops, swept) of the last batched call."""
+    pr, op, sw = C.c_uint64(), C.c_uint64(), C.c_int32()
+    h.check(h.lib.te_last_work(h.h, C.byref(pr), C.byref(op), C.byref(sw)))
+    return int(pr.value), int(op.value), bool(sw.value)

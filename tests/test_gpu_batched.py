@@ -261,3 +261,38 @@ def test_autotune_picks_a_shape_caches_it_and_keeps_results(te_handle, tmp_path)
         assert te.te_autotune(h3, ds, w.instances, w.k, cache_path=cache) == (t, q)
     finally:
         h3.close()
+
+
+@pytest.mark.parametrize("case", ["c3", "c4", "ties", "k1", "k16", "ar1", "c5"])
+def test_sorted_sweep_equals_exhaustive_search(te_handle, case):
+    if case == "c3":
+        w = I.config(3, n_t=2, S=30)
+    elif case == "c4":
+        w = I.config(4, n_pairs=6, n_t=3)
+    elif case == "ties":
+        rng = np.random.default_rng(31)
+        src = rng.integers(0, 4, size=(60, 50)).astype(np.float32)
+        tgt = rng.integers(0, 4, size=(60, 50)).astype(np.float32)
+        s = I.Series(src, tgt, d=2, tau=1, u=2, perms=I.permutations(rng, 3, 60))
+        w = I.Workload("ties", [s], [I.Instance(0, t, W, p) for t in (5, 30) for W in (1, 4) for p in (-1, 0, 2)])
+    elif case in ("k1", "k16"):
+        w = I.config(3, n_t=1, S=6, R=150)
+        w.k = 1 if case == "k1" else 16
+    elif case == "ar1":
+        w = I.ar1_analysis("unidirectional", S=4, R=20)
+    else:
+        w = I.config(5, n_t=1, S=3)
+    ds = te.to_device(w.series)
+    te.te_set_search(te_handle, False)
+    try:
+        ref = te.te_estimate(te_handle, ds, w.instances, w.k, want_counts=True)
+        ex_pairs, _, swept0 = te.te_last_work(te_handle)
+    finally:
+        te.te_set_search(te_handle, True)
+    got = te.te_estimate(te_handle, ds, w.instances, w.k, want_counts=True)
+    sw_pairs, _, swept1 = te.te_last_work(te_handle)
+    torch.cuda.synchronize()
+    assert not swept0 and swept1
+    assert torch.equal(ref["counts"], got["counts"]) and torch.equal(ref["eps"], got["eps"])
+    assert torch.max(torch.abs(ref["te"] - got["te"])).item() <= 1e-9
+    assert 0 < sw_pairs <= ex_pairs
