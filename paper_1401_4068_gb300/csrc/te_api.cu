@@ -104,6 +104,7 @@ struct Plan {
     std::vector<te::SortGroup> groups;  // sweep mode: one sorted order per (series, start, window)
     int64_t sorted_total = 0;
     int nmax = 0;
+    int n_parts = 0;                // partial sums (per CTA query block or per warp block)
     uint64_t exhaustive_pairs = 0;  // pair evaluations of the exhaustive search (both passes)
     uint64_t exhaustive_ops = 0;
     BatchedVariant var{};
@@ -350,15 +351,6 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
         return (double)A.N * A.N * (1 + 2 * A.d) > (double)B.N * B.N * (1 + 2 * B.d);
     });
     const int per = threads * qpt;
-    P->items.clear();
-    int max_items = 1;
-    for (int i : order) {
-        InstDesc& I = P->insts[i];
-        I.item_begin = (int)P->items.size();
-        I.n_items = (I.N + per - 1) / per;
-        max_items = std::max(max_items, I.n_items);
-        for (int m = 0; m < I.n_items; ++m) P->items.push_back(WorkItem{i, m * per});
-    }
     P->smem_floats = std::min(kSmemCapBytes / 4, dmaxN);
     P->smem_floats = std::max(P->smem_floats, 4 * 11);
     P->nmax = nmax;
@@ -380,6 +372,31 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
         P->exhaustive_pairs += 2ull * (uint64_t)I.N * (uint64_t)I.N;
         P->exhaustive_ops += 2ull * (uint64_t)I.N * (uint64_t)I.N * 2ull * (uint64_t)(1 + 2 * I.d);
     }
+    // work items (cost order, an instance's items contiguous) and partial-sum ranges: an instance
+    // that the sweep keeps whole in shared memory is one item whose warps each produce one part
+    // per block of 32 * qpt queries; any other instance has one part per CTA query block
+    P->items.clear();
+    int max_parts = 1;
+    int n_parts = 0;
+    for (int i : order) {
+        InstDesc& I = P->insts[i];
+        const bool fits = (int64_t)((I.N + 3) & ~3) * (1 + 2 * I.d) <= P->smem_floats;
+        I.warp_mode = (sweep && fits && !h->per_instance) ? 1 : 0;
+        I.item_begin = (int)P->items.size();
+        I.part_begin = n_parts;
+        if (I.warp_mode) {
+            I.n_items = 1;
+            I.n_parts = (I.N + 32 * qpt - 1) / (32 * qpt);
+            P->items.push_back(WorkItem{i, 0});
+        } else {
+            I.n_items = (I.N + per - 1) / per;
+            I.n_parts = I.n_items;
+            for (int m = 0; m < I.n_items; ++m) P->items.push_back(WorkItem{i, m * per});
+        }
+        n_parts += I.n_parts;
+        max_parts = std::max(max_parts, I.n_parts);
+    }
+    P->n_parts = n_parts;
     if (sweep) {
         std::map<std::tuple<const float*, int, int, int, int>, int64_t> gidx;
         for (auto& I : P->insts) {
@@ -397,7 +414,7 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
     // bound on the summation error relative to sum |terms| (see te_estimate in the header):
     // 3*qpt float-float additions per thread (<= 2^-46 each), table rounding (2^-47), FP64
     // reductions over threads and items
-    P->err_coef = 3.0 * qpt * 0x1p-46 + 0x1p-47 + (threads + max_items + 64) * 0x1p-52;
+    P->err_coef = 3.0 * qpt * 0x1p-46 + 0x1p-47 + (threads + max_parts + 64) * 0x1p-52;
     const void* fn = te::batched_kernel_ptr(P->var);
     if (!fn) return h->fail(TE_ENOTIMPL, "no kernel variant for d=%d..%d ks=%d qpt=%d", dlo, dhi, ks, qpt);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smem);
@@ -456,6 +473,7 @@ BatchArgs batch_args(te_handle* h, const Plan& P, int k, int32_t* counts, float*
     a.insts = h->d_insts.p;
     a.items = h->d_items.p;
     a.n_items = (int)P.items.size();
+    a.item_base = 0;
     a.queue = h->d_words.p;
     a.flags = h->d_words.p + 1;
     a.psi = h->d_psi.p;
@@ -492,11 +510,9 @@ te_status run_per_instance(te_handle* h, const Plan& P, int n_inst, int k, doubl
     for (int i = 0; i < n_inst; ++i) {
         const InstDesc& I = P.insts[i];
         BatchArgs ai = a;
-        ai.items = a.items + I.item_begin;
+        ai.item_base = I.item_begin;
         ai.n_items = I.n_items;
         ai.queue = h->d_words.p + 2 + i;
-        ai.partial = a.partial + I.item_begin;
-        ai.partial_abs = a.partial_abs + I.item_begin;
         if (h->profiling && i == 0 && (e = cudaEventRecord(h->ev0, stream)) != cudaSuccess)
             return h->cuda_fail(e, "event");
         if ((e = te::launch_batched(P.var, ai, std::min(I.n_items, P.grid), P.threads, P.smem, stream)) !=
@@ -532,8 +548,8 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
     if ((e = h->d_insts.ensure(P.insts.size(), &grew)) != cudaSuccess ||
         (e = h->d_items.ensure(P.items.size(), &grew)) != cudaSuccess ||
         (e = h->d_words.ensure(2 + (size_t)n_inst, &grew)) != cudaSuccess ||
-        (e = h->d_partial.ensure(P.items.size(), &grew)) != cudaSuccess ||
-        (e = h->d_partial_abs.ensure(P.items.size(), &grew)) != cudaSuccess ||
+        (e = h->d_partial.ensure((size_t)P.n_parts, &grew)) != cudaSuccess ||
+        (e = h->d_partial_abs.ensure((size_t)P.n_parts, &grew)) != cudaSuccess ||
         (n_groups > 0 && (e = h->d_te_all.ensure((size_t)n_inst, &grew)) != cudaSuccess))
         return h->fail(TE_ENOMEM, "workspace: %s", cudaGetErrorString(e));
     if ((st = prepare_sweep(h, P, &grew)) != TE_OK) return st;

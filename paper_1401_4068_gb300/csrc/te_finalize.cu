@@ -17,9 +17,9 @@ __global__ void finalize_te_kernel(const InstDesc* __restrict__ insts, int n_ins
     if (i >= n_inst) return;
     const InstDesc I = insts[i];
     double s = 0.0, sa = 0.0;
-    for (int m = 0; m < I.n_items; ++m) {
-        s += partial[I.item_begin + m];
-        sa += partial_abs[I.item_begin + m];
+    for (int m = 0; m < I.n_parts; ++m) {
+        s += partial[I.part_begin + m];
+        sa += partial_abs[I.part_begin + m];
     }
     te[i] = psi_k + s / (double)I.N;
     if (err) err[i] = sa * err_coef / (double)I.N + fabs(psi_k) * 0x1p-52;

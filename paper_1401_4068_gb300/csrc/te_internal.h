@@ -20,6 +20,10 @@ struct InstDesc {
     int64_t sort_off;      // offset of its group's sorted order in the sweep arrays (sweep mode)
     int32_t item_begin;    // its work items are item_begin .. item_begin + n_items - 1
     int32_t n_items;
+    int32_t part_begin;    // its partial sums are part_begin .. part_begin + n_parts - 1
+    int32_t n_parts;
+    int32_t warp_mode;     // 1: one item; the instance is staged once and warps take query blocks
+    int32_t pad_;
 };
 
 // Points of one (series, window start, window) group: the estimates of a group (original and
@@ -49,14 +53,15 @@ enum : int32_t { kFlagBadPerm = 1 };
 struct BatchArgs {
     const InstDesc* insts;
     const WorkItem* items;
-    int32_t n_items;
+    int32_t n_items;         // items item_base .. item_base + n_items - 1 are this launch's
+    int32_t item_base;
     int32_t* queue;          // work-queue head, zeroed before every launch
     int32_t* flags;          // device flag word (kFlag*)
     const float2* psi;       // psi(n) as (hi, lo) float pair, n = 0 .. psi_n-1 (entry 0 unused)
     int32_t k;
     int32_t smem_floats;     // floats of dynamic shared memory (reference tile capacity * D)
-    double* partial;         // [n_items] per-item sum of the Eq. 9 digamma terms
-    double* partial_abs;     // [n_items] per-item sum of |terms| (for the error bound)
+    double* partial;         // per-part sum of the Eq. 9 digamma terms (InstDesc part ranges)
+    double* partial_abs;     // per-part sum of |terms| (for the error bound)
     int32_t* counts_out;     // nullable: per instance [3][N] at 3 * pt_off
     float* eps_out;          // nullable: per instance [N] at pt_off
     const int32_t* sorted_idx;  // sweep mode: per group, point indices in ascending key order

@@ -14,20 +14,27 @@ __global__ void __launch_bounds__(kBatchedMaxThreads) batched_kernel(const Batch
     __shared__ double sred[64];
     __shared__ float sbnd[64];
     __shared__ int s_item;
+    __shared__ int s_wblock;
     for (;;) {
         __syncthreads();  // everyone is done with s_item / sred of the previous item
         if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
         __syncthreads();
-        const int it = s_item;
-        if (it >= a.n_items) break;
+        const int ticket = s_item;
+        if (ticket >= a.n_items) break;
+        const int it = a.item_base + ticket;
         const WorkItem w = a.items[it];
         const InstDesc I = a.insts[w.inst];
-#define TE_PROCESS(DD)                                                          \
-    do {                                                                        \
-        if constexpr (SWEEP)                                                    \
-            process_item_sweep<DD, Q, KS>(a, I, w.q0, it, sm, sred, sbnd);     \
-        else                                                                    \
-            process_item<DD, Q, KS>(a, I, w.q0, it, sm, sred);                  \
+        const int part = I.part_begin + (it - I.item_begin);
+#define TE_PROCESS(DD)                                                                    \
+    do {                                                                                  \
+        if constexpr (SWEEP) {                                                            \
+            if (I.warp_mode)                                                              \
+                process_instance_sweep_warps<DD, Q, KS>(a, I, sm, &s_wblock);             \
+            else                                                                          \
+                process_item_sweep<DD, Q, KS>(a, I, w.q0, part, sm, sred, sbnd);          \
+        } else {                                                                          \
+            process_item<DD, Q, KS>(a, I, w.q0, part, sm, sred);                          \
+        }                                                                                 \
     } while (0)
         if constexpr (DLO == DHI) {
             TE_PROCESS(DLO);

@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(te::kBatchedMaxThreads) na_batched_kernel(cons
     int32_t* words = reinterpret_cast<int32_t*>(p.scratch + kOffWords);
     te::BatchArgs a{};
     a.n_items = p.n_items;
+    a.item_base = 0;
     a.queue = words;
     a.flags = words + 1;
     a.psi = reinterpret_cast<const float2*>(p.scratch + kOffPsi);
@@ -121,6 +122,9 @@ __global__ void __launch_bounds__(te::kBatchedMaxThreads) na_batched_kernel(cons
         I.pt_off = 0;
         I.item_begin = g * p.items_per_inst;
         I.n_items = p.items_per_inst;
+        I.part_begin = I.item_begin;
+        I.n_parts = I.n_items;
+        I.warp_mode = 0;
         te::process_item<d, kNaQ, kNaKS>(a, I, j * (int)blockDim.x * kNaQ, it, sm, sred);
     }
 }

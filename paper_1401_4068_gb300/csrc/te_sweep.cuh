@@ -342,4 +342,134 @@ __device__ __forceinline__ void process_item_sweep(const BatchArgs& a, const Ins
     }
 }
 
+// first position p in [0, n) of the shared-memory key row with key > x (keys ascending)
+__device__ __forceinline__ int smem_first_greater(const float* __restrict__ key, int n, float x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (key[mid] > x) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+// One warp's block of 32*Q consecutive sorted queries of an instance staged whole in shared
+// memory: pass 1 (own block, then right, then left), pass 2 over the key window, digamma terms;
+// the block's partial sum is written to part. No CTA-wide barrier.
+template <int d, int Q, int KS>
+__device__ __forceinline__ void sweep_warp_block(const BatchArgs& a, const InstDesc& I, const float* sm, int ldt,
+                                                 int wb, int part) {
+    constexpr int D = 1 + 2 * d;
+    const int N = I.N;
+    const int lane = threadIdx.x & 31;
+    const int32_t* sidx = a.sorted_idx + I.sort_off;
+    const int wbase = wb * 32 * Q;
+    u64 qq[Q][D];
+    float qkey[Q];
+    int qidx[Q];
+    bool qv[Q];
+    int nvalid = 0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int pos = wbase + q * 32 + lane;
+        qv[q] = pos < N;
+        qidx[q] = qv[q] ? __ldg(sidx + pos) : -1;
+        // the staged tile holds the sorted points: read the query's coordinates from it
+#pragma unroll
+        for (int c = 0; c < D; ++c) qq[q][c] = dup2(qv[q] ? sm[c * ldt + pos] : 0.0f);
+        qkey[q] = qv[q] ? sm[ldt + pos] : 0.0f;
+        nvalid += __popc(__ballot_sync(0xffffffffu, qv[q]));
+    }
+    const int ng = (N + 3) >> 2;
+    unsigned long long groups_done = 0;
+    float t[Q][KS];
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int m = 0; m < KS; ++m) t[q][m] = f_inf();
+    bool done = false;
+    const int g_own0 = wbase >> 2;
+    const int g_own1 = min(ng, (min(wbase + 32 * Q, N) + 3) >> 2);
+    groups_done += knn_range<D, Q, KS>(sm, ldt, g_own0, g_own1, 0, qq, qkey, qv, t, done);
+    groups_done += knn_range<D, Q, KS>(sm, ldt, g_own1, ng, +1, qq, qkey, qv, t, done);
+    groups_done += knn_range<D, Q, KS>(sm, ldt, 0, g_own0, -1, qq, qkey, qv, t, done);
+    float e[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) e[q] = topk_select(t[q], a.k);
+
+    float cz[Q], cyz[Q], cxz[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) cz[q] = cyz[q] = cxz[q] = 0.0f;
+    float lb, rb;
+    warp_window(qkey, qv, e, lb, rb);
+    const int g_lo = smem_first_greater(sm + ldt, N, lb) >> 2;
+    groups_done += count_range<d, d, Q>(sm, ldt, g_lo, ng, lb, rb, qq, e, cz, cyz, cxz);
+
+    FF acc{0.0f, 0.0f};
+    float acc_abs = 0.0f;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        if (qv[q]) {
+            const int i = qidx[q];
+            const int self = e[q] > 0.0f ? 1 : 0;
+            const int nz = (int)cz[q] - self, nyz = (int)cyz[q] - self, nxz = (int)cxz[q] - self;
+            if (a.counts_out) {
+                int32_t* co = a.counts_out + 3 * I.pt_off;
+                co[i] = nz;
+                co[N + i] = nyz;
+                co[2 * N + i] = nxz;
+            }
+            if (a.eps_out) a.eps_out[I.pt_off + i] = e[q];
+            const float2 p1 = __ldg(a.psi + nz + 1);
+            const float2 p2 = __ldg(a.psi + nyz + 1);
+            const float2 p3 = __ldg(a.psi + nxz + 1);
+            acc = ff_add(acc, p1.x, p1.y);
+            acc = ff_add(acc, -p2.x, -p2.y);
+            acc = ff_add(acc, -p3.x, -p3.y);
+            acc_abs += fabsf(p1.x) + fabsf(p2.x) + fabsf(p3.x);
+        }
+    }
+    double v = (double)acc.hi + (double)acc.lo;
+    double w = (double)acc_abs;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v += __shfl_down_sync(0xffffffffu, v, o);
+        w += __shfl_down_sync(0xffffffffu, w, o);
+    }
+    if (lane == 0) {
+        a.partial[part] = v;
+        a.partial_abs[part] = w;
+        if (a.exec) {
+            const unsigned long long pairs = groups_done * 4ull * (unsigned long long)nvalid;
+            atomicAdd(a.exec, pairs);
+            atomicAdd(a.exec + 1, pairs * 2ull * D);
+        }
+    }
+}
+
+// A whole instance that fits shared memory: staged once in sorted order, then every warp takes
+// blocks of 32*Q queries from a CTA-local counter until none is left (work balances across the
+// warps; the only barriers are at the start and the end of the instance).
+template <int d, int Q, int KS>
+__device__ __forceinline__ void process_instance_sweep_warps(const BatchArgs& a, const InstDesc& I, float* sm,
+                                                             int* s_wblock) {
+    constexpr int D = 1 + 2 * d;
+    const int N = I.N;
+    const int ldt = (N + 3) & ~3;
+    const int32_t* sidx = a.sorted_idx + I.sort_off;
+    stage_tile_sorted<d>(I, sidx, 0, N, ldt, sm, a.flags);
+    if (threadIdx.x == 0) *s_wblock = 0;
+    __syncthreads();
+    const int nwb = (N + 32 * Q - 1) / (32 * Q);
+    for (;;) {
+        int wb = 0;
+        if ((threadIdx.x & 31) == 0) wb = atomicAdd(s_wblock, 1);
+        wb = __shfl_sync(0xffffffffu, wb, 0);
+        if (wb >= nwb) break;
+        sweep_warp_block<d, Q, KS>(a, I, sm, ldt, wb, I.part_begin + wb);
+    }
+    __syncthreads();  // the staged instance stays until every warp is done with it
+    (void)D;
+}
+
 }  // namespace te
