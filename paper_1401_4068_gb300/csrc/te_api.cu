@@ -30,6 +30,7 @@ constexpr int kMaxEmbedDim = 15;      // te_embed: D = 1 + 2d <= 31
 constexpr int kMaxBatchedD = 5;       // te_estimate / te_surrogate_test
 constexpr int kSmemCapBytes = 64 * 1024;  // reference tile budget of the batched kernel
 constexpr int kSweepSmemMaxBytes = 160 * 1024;  // sweep mode: room for whole query blocks per tile
+constexpr int64_t kResidentMaxBytes = 200 * 1024;  // sweep mode: whole instances in shared memory
 
 std::string g_create_error;
 
@@ -358,13 +359,19 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
     // block per tile (its queries then lie in one tile)
     bool sweep = h->search_mode == 1 && nmax <= te::kSweepMaxN;
     if (sweep) {
-        int need = P->smem_floats;
-        for (const auto& I : P->insts) {
-            const int D = 1 + 2 * I.d;
-            if ((int64_t)((I.N + 3) & ~3) * D > P->smem_floats) need = std::max(need, per * D);
+        // every instance resident in shared memory (up to kResidentMaxBytes) when it fits there,
+        // which lets warps balance the work; otherwise tiles of whole CTA query blocks
+        if (!h->per_instance && (int64_t)dmaxN * (int64_t)sizeof(float) <= kResidentMaxBytes) {
+            P->smem_floats = std::max(P->smem_floats, dmaxN);
+        } else {
+            int need = P->smem_floats;
+            for (const auto& I : P->insts) {
+                const int D = 1 + 2 * I.d;
+                if ((int64_t)((I.N + 3) & ~3) * D > P->smem_floats) need = std::max(need, per * D);
+            }
+            if (need * (int)sizeof(float) > kSweepSmemMaxBytes) sweep = false;
+            else P->smem_floats = need;
         }
-        if (need * (int)sizeof(float) > kSweepSmemMaxBytes) sweep = false;
-        else P->smem_floats = need;
     }
     P->var.sweep = sweep;
     P->smem = (size_t)P->smem_floats * sizeof(float);
@@ -378,6 +385,9 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
     P->items.clear();
     int max_parts = 1;
     int n_parts = 0;
+    // warp mode splits an instance into several items when the batch alone would not give every
+    // SM a few items (each item stages the instance and takes a share of its warp blocks)
+    const int want_items = 4 * h->sm_count;
     for (int i : order) {
         InstDesc& I = P->insts[i];
         const bool fits = (int64_t)((I.N + 3) & ~3) * (1 + 2 * I.d) <= P->smem_floats;
@@ -385,9 +395,12 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
         I.item_begin = (int)P->items.size();
         I.part_begin = n_parts;
         if (I.warp_mode) {
-            I.n_items = 1;
-            I.n_parts = (I.N + 32 * qpt - 1) / (32 * qpt);
-            P->items.push_back(WorkItem{i, 0});
+            const int nwb = (I.N + 32 * qpt - 1) / (32 * qpt);
+            const int split = std::max(1, std::min(nwb, (want_items + n_inst - 1) / n_inst));
+            I.wb_chunk = (nwb + split - 1) / split;
+            I.n_items = (nwb + I.wb_chunk - 1) / I.wb_chunk;
+            I.n_parts = nwb;
+            for (int m = 0; m < I.n_items; ++m) P->items.push_back(WorkItem{i, m * I.wb_chunk});
         } else {
             I.n_items = (I.N + per - 1) / per;
             I.n_parts = I.n_items;

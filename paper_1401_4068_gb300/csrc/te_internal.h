@@ -22,8 +22,8 @@ struct InstDesc {
     int32_t n_items;
     int32_t part_begin;    // its partial sums are part_begin .. part_begin + n_parts - 1
     int32_t n_parts;
-    int32_t warp_mode;     // 1: one item; the instance is staged once and warps take query blocks
-    int32_t pad_;
+    int32_t warp_mode;     // 1: the instance is staged whole and warps take 32*Q-query blocks
+    int32_t wb_chunk;      // warp mode: warp blocks per work item (an item's q0 is its first block)
 };
 
 // Points of one (series, window start, window) group: the estimates of a group (original and

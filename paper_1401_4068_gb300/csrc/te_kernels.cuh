@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(kBatchedMaxThreads) batched_kernel(const Batch
     do {                                                                                  \
         if constexpr (SWEEP) {                                                            \
             if (I.warp_mode)                                                              \
-                process_instance_sweep_warps<DD, Q, KS>(a, I, sm, &s_wblock);             \
+                process_instance_sweep_warps<DD, Q, KS>(a, I, w.q0, sm, &s_wblock);       \
             else                                                                          \
                 process_item_sweep<DD, Q, KS>(a, I, w.q0, part, sm, sred, sbnd);          \
         } else {                                                                          \

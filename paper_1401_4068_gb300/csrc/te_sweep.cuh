@@ -451,21 +451,21 @@ __device__ __forceinline__ void sweep_warp_block(const BatchArgs& a, const InstD
 // blocks of 32*Q queries from a CTA-local counter until none is left (work balances across the
 // warps; the only barriers are at the start and the end of the instance).
 template <int d, int Q, int KS>
-__device__ __forceinline__ void process_instance_sweep_warps(const BatchArgs& a, const InstDesc& I, float* sm,
-                                                             int* s_wblock) {
+__device__ __forceinline__ void process_instance_sweep_warps(const BatchArgs& a, const InstDesc& I, int wb0,
+                                                             float* sm, int* s_wblock) {
     constexpr int D = 1 + 2 * d;
     const int N = I.N;
     const int ldt = (N + 3) & ~3;
     const int32_t* sidx = a.sorted_idx + I.sort_off;
     stage_tile_sorted<d>(I, sidx, 0, N, ldt, sm, a.flags);
-    if (threadIdx.x == 0) *s_wblock = 0;
+    if (threadIdx.x == 0) *s_wblock = wb0;
     __syncthreads();
-    const int nwb = (N + 32 * Q - 1) / (32 * Q);
+    const int wb1 = min((N + 32 * Q - 1) / (32 * Q), wb0 + I.wb_chunk);  // this item's warp blocks
     for (;;) {
         int wb = 0;
         if ((threadIdx.x & 31) == 0) wb = atomicAdd(s_wblock, 1);
         wb = __shfl_sync(0xffffffffu, wb, 0);
-        if (wb >= nwb) break;
+        if (wb >= wb1) break;
         sweep_warp_block<d, Q, KS>(a, I, sm, ldt, wb, I.part_begin + wb);
     }
     __syncthreads();  // the staged instance stays until every warp is done with it
