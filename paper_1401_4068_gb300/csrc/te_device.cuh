@@ -108,6 +108,39 @@ __device__ __forceinline__ void load_refs4(const float* __restrict__ s, int ldt,
     for (int c = 0; c < D; ++c) r[c] = *reinterpret_cast<const ulonglong2*>(s + c * ldt + 4 * j);
 }
 
+// Pass-1 step for four references against the thread's Q queries. For D >= 5 every distance
+// is computed before the first (branching) top-k insertion, which leaves the scheduler more
+// independent work across the branches; for D = 3 the interleaved order measures faster.
+template <int D, int Q, int KS>
+__device__ __forceinline__ void knn_step4(const u64 (&qq)[Q][D], const ulonglong2 (&r)[D], float (&t)[Q][KS]) {
+    if constexpr (D <= 3) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            float dx[D], dy[D], dz[D], dw[D];
+            diff4<D>(qq[q], r, dx, dy, dz, dw);
+            topk_push(t[q], absmax_range<0, D - 1>(dx));
+            topk_push(t[q], absmax_range<0, D - 1>(dy));
+            topk_push(t[q], absmax_range<0, D - 1>(dz));
+            topk_push(t[q], absmax_range<0, D - 1>(dw));
+        }
+    } else {
+        float m[Q][4];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            float dx[D], dy[D], dz[D], dw[D];
+            diff4<D>(qq[q], r, dx, dy, dz, dw);
+            m[q][0] = absmax_range<0, D - 1>(dx);
+            m[q][1] = absmax_range<0, D - 1>(dy);
+            m[q][2] = absmax_range<0, D - 1>(dz);
+            m[q][3] = absmax_range<0, D - 1>(dw);
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) topk_push(t[q], m[q][e]);
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // Pass 1 over one staged reference tile: smem holds coordinate c of reference j at
 // s[c * ldt + j] (structure of arrays, +inf past the last valid reference). Every thread
@@ -121,15 +154,7 @@ __device__ __forceinline__ void knn_tile(const float* __restrict__ s, int ldt, i
     for (int j = 0; j < n4; ++j) {
         ulonglong2 r[D];
         load_refs4<D>(s, ldt, j, r);
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            float dx[D], dy[D], dz[D], dw[D];
-            diff4<D>(qq[q], r, dx, dy, dz, dw);
-            topk_push(t[q], absmax_range<0, D - 1>(dx));
-            topk_push(t[q], absmax_range<0, D - 1>(dy));
-            topk_push(t[q], absmax_range<0, D - 1>(dz));
-            topk_push(t[q], absmax_range<0, D - 1>(dw));
-        }
+        knn_step4<D, Q, KS>(qq, r, t);
     }
 }
 
@@ -143,11 +168,13 @@ __device__ __forceinline__ void knn_tile(const float* __restrict__ s, int ldt, i
 template <int DY, int DX>
 __device__ __forceinline__ void count_one(const float (&d)[1 + DY + DX], float e, float& cz, float& cyz,
                                           float& cxz) {
-    const float b = absmax_range<1, DY>(d);
-    const float x = absmax_range<DY + 1, DY + DX>(d);
-    const float sb = set_lt(b, e);
+    // a group of one coordinate needs no maximum: compare |d| directly
+    float sb, sx;
+    if constexpr (DY == 1) sb = abs_set_lt(d[1], e);
+    else sb = set_lt(absmax_range<1, DY>(d), e);
+    if constexpr (DX == 1) sx = abs_set_lt(d[DY + 1], e);
+    else sx = set_lt(absmax_range<DY + 1, DY + DX>(d), e);
     const float sa = abs_set_lt(d[0], e);
-    const float sx = set_lt(x, e);
     cz += sb;
     cyz = fmaf(sa, sb, cyz);
     cxz = fmaf(sx, sb, cxz);

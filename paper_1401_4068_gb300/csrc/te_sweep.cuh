@@ -95,15 +95,7 @@ __device__ __forceinline__ void knn_group(const float* __restrict__ s, int ldt, 
                                           float (&t)[Q][KS]) {
     ulonglong2 r[D];
     load_refs4<D>(s, ldt, j, r);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        float dx[D], dy[D], dz[D], dw[D];
-        diff4<D>(qq[q], r, dx, dy, dz, dw);
-        topk_push(t[q], absmax_range<0, D - 1>(dx));
-        topk_push(t[q], absmax_range<0, D - 1>(dy));
-        topk_push(t[q], absmax_range<0, D - 1>(dz));
-        topk_push(t[q], absmax_range<0, D - 1>(dw));
-    }
+    knn_step4<D, Q, KS>(qq, r, t);
 }
 
 // pass 1 over groups [g0, g1) of the staged tile: dir 0 evaluates all of them (the warp's own
