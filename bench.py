@@ -37,7 +37,7 @@ METRIC = "max-norm pair evals/s & TE estimates/s (incl. surrogates), batched vs 
 FLUSH_BYTES = 256 << 20          # > 129 MB L2: written between timed steps
 FALLBACK_SM_MHZ = 2070.0
 ALU_LANES_PER_SM = 128           # FP32 lanes per SM (4 SMSPs x 32)
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "batched_kernel_traffic.json")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "{kernel}_traffic.json")
 
 WORKLOADS = {
     "c3": dict(cid=3, kw={}, desc="C3 surrogate test: AR(2) X->Y, 400 trials, d=3, tau=1, u=5, W=3 "
@@ -164,13 +164,13 @@ def measured_peaks():
         return {}
 
 
-def traffic_per_launch(w):
-    """DRAM bytes of one persistent-kernel launch from the committed ncu summary (a smaller
-    capture of the same instance shape, scaled by the number of estimates, since every estimate
-    stages the same points), or None when absent, taken on another instance shape, or taken on
-    different kernel sources."""
+def traffic_per_launch(w, kernel):
+    """DRAM bytes of one launch of `kernel` from the committed ncu summary (a capture of the same
+    instance shape, scaled by the number of estimates, since every estimate stages the same
+    points), or None when absent, taken on another instance shape, or taken on different kernel
+    sources."""
     try:
-        with open(PROFILE_TRAFFIC) as f:
+        with open(PROFILE_TRAFFIC.format(kernel=kernel)) as f:
             prof = json.load(f)
     except (OSError, ValueError):
         return None
@@ -233,6 +233,7 @@ def bench_ours(args):
     ds = te.to_device(w.series, dev)
     te.te_set_profiling(h, True)
     te.te_set_search(h, not args.exhaustive)
+    te.te_set_sharing(h, not args.no_sharing)
 
     def step(series_dev, outs=None):
         if scan:
@@ -294,6 +295,7 @@ def bench_ours(args):
     barrier()
     clocks = sampler.stop()
     exec_pairs, exec_ops, swept = te.te_last_work(h)
+    alu_ops, bundles = te.te_last_alu_ops(h)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     if ws > 1:
@@ -307,10 +309,12 @@ def bench_ours(args):
     value = ws * pe_step * args.steps / (total_ms / 1e3)
     te_rate = ws * n_est * args.steps / (total_ms / 1e3)
 
-    # ---- roofline of the persistent kernel (CUDA events on its own stream, live)
+    # ---- roofline of the search kernel (CUDA events on its own stream, live): the bundle kernel
+    # when target-part sharing formed bundles, else the persistent batched kernel
     kms = statistics.mean(kernel_ms)
-    ops = exec_ops  # FP32 operations the kernel executed (device-counted by the sweep)
+    ops = exec_ops  # 2 D FP32 operations per evaluated (query, reference, estimate) pair
     achieved = ops / (kms / 1e3) / 1e12
+    kernel = "bundle_kernel" if bundles else "batched_kernel"
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz") or FALLBACK_SM_MHZ)
     n_sm = props.multi_processor_count
@@ -320,8 +324,12 @@ def bench_ours(args):
             "peak_source": f"{n_sm} SMs x {ALU_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
                            f"({'MEASURED_PEAKS.json sm_max_mhz' if peaks.get('sm_max_mhz') else 'fallback clock'})",
             "op": "FP32 subtract or abs-max, 2*D per evaluated (query, reference) pair, both passes",
-            "kernel": "batched_kernel", "kernel_ms": round(kms, 4),
-            "traffic": traffic_per_launch(w)}
+            "kernel": kernel, "kernel_ms": round(kms, 4),
+            "traffic": traffic_per_launch(w, kernel),
+            # what the ALU actually executed: with target-part sharing the target part's 2 (1 + d)
+            # operations of a pair run once per bundle of estimates
+            "alu_ops_executed": alu_ops,
+            "alu_frac_executed": round(alu_ops / (kms / 1e3) / 1e12 / peak, 4)}
     if clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = round(achieved / (n_sm * ALU_LANES_PER_SM * clocks["sm_mhz"] * 1e6 / 1e12), 4)
 
@@ -441,7 +449,9 @@ def bench_ours(args):
         "te_estimates_per_s": te_rate,
         "search": {"mode": "sorted sweep" if swept else "exhaustive",
                    "pair_evals_executed_per_step": exec_pairs,
-                   "executed_vs_algorithmic": round(exec_pairs / max(1, pe_step), 4)},
+                   "executed_vs_algorithmic": round(exec_pairs / max(1, pe_step), 4),
+                   "target_part_sharing": {"bundles": bundles, "alu_ops_executed_per_step": alu_ops,
+                                           "alu_ops_vs_2D_per_pair": round(alu_ops / max(1, exec_ops), 4)}},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks, "per_launch": per,
         "batched_vs_per_launch": None if per is None else per["batched_vs_per_launch"],
@@ -501,6 +511,7 @@ def main():
     ap.add_argument("--no-per-launch", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--exhaustive", action="store_true", help="exhaustive search instead of the sorted sweep")
+    ap.add_argument("--no-sharing", action="store_true", help="no target-part sharing across estimates")
     ap.add_argument("--shape", default=None, help="fixed launch shape THREADSxQPT instead of autotuning")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

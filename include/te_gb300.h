@@ -216,6 +216,23 @@ te_status te_set_search(te_handle* h, int32_t mode);
  * `swept` (nullable) is 1 when the sweep ran. */
 te_status te_last_work(te_handle* h, uint64_t* pairs, uint64_t* ops, int32_t* swept);
 
+/* Target-part sharing in the sorted sweep (enable = 1, the default; results are identical):
+ * estimates whose joint points share the target part y_t, y- (same target series, repetitions,
+ * window start, window, d and tau; they differ only in the source part x-: the original and its
+ * trial-shuffled surrogates of Fig. 3, and every scanned delay u of Eq. 5) are processed in
+ * bundles of up to 4 that fit shared memory together. A bundle is staged once and the target
+ * part of every distance and count is computed once for all of its members. The paper computes
+ * each surrogate separately; this is exact because max is exact: each member sees the same FP32
+ * differences the unshared search computes. Applies with k <= 4 to one embedding dimension per
+ * batch (the most frequent among shareable estimates); every other estimate runs unshared. */
+te_status te_set_sharing(te_handle* h, int32_t enable);
+
+/* FP32 operations the kernels of the last te_estimate / te_surrogate_test / te_delay_scan call
+ * executed: te_last_work's ops minus those target-part sharing saved (the same as te_last_work's
+ * ops without sharing). `bundles` (nullable): the number of bundles formed. The sweep's counters
+ * are read from the device (synchronises the device). */
+te_status te_last_alu_ops(te_handle* h, uint64_t* ops, int32_t* bundles);
+
 /* Batching mode of te_estimate / te_surrogate_test. per_instance = 0 (default): one persistent
  * launch for the whole batch, captured in a CUDA graph. per_instance = 1: the same kernel and
  * tables, launched once per instance with a grid of that instance's work items and no graph,

@@ -113,6 +113,11 @@ struct Plan {
     size_t smem = 0;
     double err_coef = 0;
     int64_t n_points = 0;
+    // bundle kernel (target-part sharing): its work items, member lists, d and launch shape
+    std::vector<WorkItem> bitems;
+    std::vector<int32_t> members;
+    int bd = 0, bgrid = 0, n_bundled = 0;
+    size_t bsmem = 0;
 };
 
 struct DeviceGuard {
@@ -148,8 +153,10 @@ struct te_handle {
     std::map<std::string, std::pair<int, int>> tuned;  // batch signature -> (threads, qpt)
     bool per_instance = false;  // one launch per instance instead of one persistent launch
     int search_mode = 1;        // 1: sorted sweep where it applies, 0: exhaustive search
+    bool sharing = true;        // bundles of estimates with one target part (sweep mode)
     bool last_sweep = false;
     uint64_t last_pairs = 0, last_ops = 0;
+    int last_bundled = 0;
 
     DevBuf<InstDesc> d_insts;
     DevBuf<WorkItem> d_items;
@@ -160,6 +167,8 @@ struct te_handle {
     DevBuf<int32_t> d_sidx;
     DevBuf<float> d_skey;
     DevBuf<unsigned long long> d_exec;
+    DevBuf<WorkItem> d_bitems;
+    DevBuf<int32_t> d_members;
     HostBuf<unsigned char> h_stage;
     int workspace_gen = 0;
 
@@ -383,12 +392,76 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
     // that the sweep keeps whole in shared memory is one item whose warps each produce one part
     // per block of 32 * qpt queries; any other instance has one part per CTA query block
     P->items.clear();
-    int max_parts = 1;
-    int n_parts = 0;
     // warp mode splits an instance into several items when the batch alone would not give every
     // SM a few items (each item stages the instance and takes a share of its warp blocks)
     const int want_items = 4 * h->sm_count;
+    int max_parts = 1;
+    int n_parts = 0;
+    // target-part sharing: estimates with one target part (target series, repetitions, window
+    // start, window, d, tau) that fit shared memory together form bundles of up to kBundleMax
+    // (no bundle of one), processed by the bundle kernel; one embedding dimension per batch
+    std::vector<char> bundled(n_inst, 0);
+    if (sweep && h->sharing && !h->per_instance && ks == 5) {
+        std::map<std::tuple<const float*, int, int, int, int, int, int>, std::vector<int>> by_target;
+        for (int i = 0; i < n_inst; ++i) {
+            const InstDesc& I = P->insts[i];
+            by_target[std::make_tuple(I.tgt, I.T, I.R, I.t_start, I.W, I.d, I.tau)].push_back(i);
+        }
+        int64_t shareable[kMaxBatchedD + 1] = {0};  // estimates in groups of >= 2 that fit, per d
+        for (const auto& kv : by_target)
+            if (kv.second.size() >= 2) {
+                const InstDesc& I = P->insts[kv.second[0]];
+                const int64_t bytes = (int64_t)((I.N + 3) & ~3) * (1 + I.d + te::kBundleMax * I.d) * 4;
+                if (bytes <= kResidentMaxBytes) shareable[I.d] += (int64_t)kv.second.size();
+            }
+        for (int d = 1; d <= kMaxBatchedD; ++d)
+            if (shareable[d] > (P->bd ? shareable[P->bd] : 0)) P->bd = d;
+        int n_bundles = 0;
+        for (const auto& kv : by_target) {
+            const InstDesc& I0 = P->insts[kv.second[0]];
+            const int64_t bytes = (int64_t)((I0.N + 3) & ~3) * (1 + I0.d + te::kBundleMax * I0.d) * 4;
+            if (kv.second.size() < 2 || I0.d != P->bd || bytes > kResidentMaxBytes) continue;
+            P->bsmem = std::max(P->bsmem, (size_t)bytes);
+            n_bundles += (int)((kv.second.size() + te::kBundleMax - 1) / te::kBundleMax);
+        }
+        const int per_b = 32 * te::kBundleQ;
+        for (const auto& kv : by_target) {
+            const std::vector<int>& v = kv.second;
+            const InstDesc& I0 = P->insts[v[0]];
+            const int64_t bytes = (int64_t)((I0.N + 3) & ~3) * (1 + I0.d + te::kBundleMax * I0.d) * 4;
+            if (v.size() < 2 || I0.d != P->bd || bytes > kResidentMaxBytes) continue;
+            const int nwb = (I0.N + per_b - 1) / per_b;
+            const int split = std::max(1, std::min(nwb, (want_items + n_bundles - 1) / std::max(1, n_bundles)));
+            const int chunk = (nwb + split - 1) / split;
+            size_t pos = 0;
+            while (pos < v.size()) {
+                size_t nb = std::min<size_t>(te::kBundleMax, v.size() - pos);
+                if (v.size() - pos - nb == 1) nb -= 1;  // leave two for the last bundle, not one
+                InstDesc& L = P->insts[v[pos]];
+                L.bundle_n = (int)nb;
+                L.bundle_off = (int)P->members.size();
+                L.wb_chunk = chunk;
+                for (size_t m = 0; m < nb; ++m) {
+                    const int i = v[pos + m];
+                    InstDesc& I = P->insts[i];
+                    P->members.push_back(i);
+                    bundled[i] = 1;
+                    I.warp_mode = 1;
+                    I.item_begin = 0;
+                    I.n_items = 0;
+                    I.part_begin = n_parts;
+                    I.n_parts = nwb;
+                    n_parts += nwb;
+                    max_parts = std::max(max_parts, nwb);
+                }
+                for (int c = 0; c * chunk < nwb; ++c) P->bitems.push_back(WorkItem{v[pos], c * chunk});
+                pos += nb;
+                ++P->n_bundled;
+            }
+        }
+    }
     for (int i : order) {
+        if (bundled[i]) continue;
         InstDesc& I = P->insts[i];
         const bool fits = (int64_t)((I.N + 3) & ~3) * (1 + 2 * I.d) <= P->smem_floats;
         I.warp_mode = (sweep && fits && !h->per_instance) ? 1 : 0;
@@ -437,6 +510,18 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
     if (e != cudaSuccess) return h->cuda_fail(e, "occupancy query");
     if (per_sm < 1) return h->fail(TE_ENOTIMPL, "batched kernel does not fit: threads=%d smem=%zu", threads, P->smem);
     P->grid = (int)std::min<int64_t>((int64_t)per_sm * h->sm_count, (int64_t)P->items.size());
+    if (!P->bitems.empty()) {
+        const void* bf = te::bundle_kernel_ptr(P->bd, ks);
+        if (!bf) return h->fail(TE_ENOTIMPL, "no bundle kernel for d=%d ks=%d", P->bd, ks);
+        if ((e = cudaFuncSetAttribute(bf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->bsmem)) != cudaSuccess)
+            return h->cuda_fail(e, "cudaFuncSetAttribute (bundle)");
+        int bper = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bper, bf, te::kBundleThreads, P->bsmem)) !=
+            cudaSuccess)
+            return h->cuda_fail(e, "occupancy query (bundle)");
+        if (bper < 1) return h->fail(TE_ENOTIMPL, "bundle kernel does not fit: smem=%zu", P->bsmem);
+        P->bgrid = (int)std::min<int64_t>((int64_t)bper * h->sm_count, (int64_t)P->bitems.size());
+    }
     (void)nmax;
     return TE_OK;
 }
@@ -445,15 +530,23 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
 te_status upload_tables(te_handle* h, const Plan& P, cudaStream_t stream) {
     const size_t bi = P.insts.size() * sizeof(InstDesc), bt = P.items.size() * sizeof(WorkItem);
     const size_t bg = P.groups.size() * sizeof(te::SortGroup);
+    const size_t bb = P.bitems.size() * sizeof(WorkItem), bm = P.members.size() * sizeof(int32_t);
     cudaError_t e;
     if ((e = cudaEventSynchronize(h->upload_done)) != cudaSuccess) return h->cuda_fail(e, "staging reuse");
-    if ((e = h->h_stage.ensure(bi + bt + bg)) != cudaSuccess) return h->fail(TE_ENOMEM, "pinned staging");
-    std::memcpy(h->h_stage.p, P.insts.data(), bi);
-    std::memcpy(h->h_stage.p + bi, P.items.data(), bt);
-    if (bg) std::memcpy(h->h_stage.p + bi + bt, P.groups.data(), bg);
-    if ((e = cudaMemcpyAsync(h->d_insts.p, h->h_stage.p, bi, cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(h->d_items.p, h->h_stage.p + bi, bt, cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
-        (bg && (e = cudaMemcpyAsync(h->d_groups.p, h->h_stage.p + bi + bt, bg, cudaMemcpyHostToDevice, stream)) !=
+    if ((e = h->h_stage.ensure(bi + bt + bg + bb + bm)) != cudaSuccess) return h->fail(TE_ENOMEM, "pinned staging");
+    unsigned char* hs = h->h_stage.p;
+    std::memcpy(hs, P.insts.data(), bi);
+    if (bt) std::memcpy(hs + bi, P.items.data(), bt);
+    if (bg) std::memcpy(hs + bi + bt, P.groups.data(), bg);
+    if (bb) std::memcpy(hs + bi + bt + bg, P.bitems.data(), bb);
+    if (bm) std::memcpy(hs + bi + bt + bg + bb, P.members.data(), bm);
+    if ((e = cudaMemcpyAsync(h->d_insts.p, hs, bi, cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
+        (bt && (e = cudaMemcpyAsync(h->d_items.p, hs + bi, bt, cudaMemcpyHostToDevice, stream)) != cudaSuccess) ||
+        (bg && (e = cudaMemcpyAsync(h->d_groups.p, hs + bi + bt, bg, cudaMemcpyHostToDevice, stream)) !=
+                   cudaSuccess) ||
+        (bb && (e = cudaMemcpyAsync(h->d_bitems.p, hs + bi + bt + bg, bb, cudaMemcpyHostToDevice, stream)) !=
+                   cudaSuccess) ||
+        (bm && (e = cudaMemcpyAsync(h->d_members.p, hs + bi + bt + bg + bb, bm, cudaMemcpyHostToDevice, stream)) !=
                    cudaSuccess) ||
         (e = cudaEventRecord(h->upload_done, stream)) != cudaSuccess)
         return h->cuda_fail(e, "table upload");
@@ -467,7 +560,9 @@ te_status prepare_sweep(te_handle* h, const Plan& P, bool* grew) {
     if ((e = h->d_groups.ensure(P.groups.size(), grew)) != cudaSuccess ||
         (e = h->d_sidx.ensure((size_t)P.sorted_total, grew)) != cudaSuccess ||
         (e = h->d_skey.ensure((size_t)P.sorted_total, grew)) != cudaSuccess ||
-        (e = h->d_exec.ensure(2, grew)) != cudaSuccess)
+        (e = h->d_exec.ensure(3, grew)) != cudaSuccess ||
+        (e = h->d_bitems.ensure(P.bitems.size(), grew)) != cudaSuccess ||
+        (e = h->d_members.ensure(P.members.size(), grew)) != cudaSuccess)
         return h->fail(TE_ENOMEM, "sweep workspace: %s", cudaGetErrorString(e));
     if ((e = te::prepare_sort_kernel(P.nmax)) != cudaSuccess) return h->cuda_fail(e, "sort kernel attribute");
     return TE_OK;
@@ -476,7 +571,7 @@ te_status prepare_sweep(te_handle* h, const Plan& P, bool* grew) {
 // the sweep's pre-pass (work counters cleared, groups sorted) on `s`
 cudaError_t launch_sweep_prepass(te_handle* h, const Plan& P, cudaStream_t s) {
     if (!P.var.sweep) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(h->d_exec.p, 0, 2 * sizeof(unsigned long long), s);
+    cudaError_t e = cudaMemsetAsync(h->d_exec.p, 0, 3 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     return te::launch_sort_groups(h->d_groups.p, (int)P.groups.size(), P.nmax, h->d_sidx.p, h->d_skey.p, s);
 }
@@ -500,6 +595,7 @@ BatchArgs batch_args(te_handle* h, const Plan& P, int k, int32_t* counts, float*
         a.sorted_idx = h->d_sidx.p;
         a.sorted_key = h->d_skey.p;
         a.exec = h->d_exec.p;
+        a.members = h->d_members.p;
     }
     return a;
 }
@@ -512,7 +608,7 @@ te_status run_per_instance(te_handle* h, const Plan& P, int n_inst, int k, doubl
     te_status st = upload_tables(h, P, stream);
     if (st != TE_OK) return st;
     h->drop_graph();
-    cudaError_t e = cudaMemsetAsync(h->d_words.p + 2, 0, (size_t)n_inst * sizeof(int32_t), stream);
+    cudaError_t e = cudaMemsetAsync(h->d_words.p + 3, 0, (size_t)n_inst * sizeof(int32_t), stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "clear queues");
     const BatchArgs a = batch_args(h, P, k, counts, eps);
     int launches = 0;
@@ -525,7 +621,7 @@ te_status run_per_instance(te_handle* h, const Plan& P, int n_inst, int k, doubl
         BatchArgs ai = a;
         ai.item_base = I.item_begin;
         ai.n_items = I.n_items;
-        ai.queue = h->d_words.p + 2 + i;
+        ai.queue = h->d_words.p + 3 + i;
         if (h->profiling && i == 0 && (e = cudaEventRecord(h->ev0, stream)) != cudaSuccess)
             return h->cuda_fail(e, "event");
         if ((e = te::launch_batched(P.var, ai, std::min(I.n_items, P.grid), P.threads, P.smem, stream)) !=
@@ -560,7 +656,7 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
     cudaError_t e;
     if ((e = h->d_insts.ensure(P.insts.size(), &grew)) != cudaSuccess ||
         (e = h->d_items.ensure(P.items.size(), &grew)) != cudaSuccess ||
-        (e = h->d_words.ensure(2 + (size_t)n_inst, &grew)) != cudaSuccess ||
+        (e = h->d_words.ensure(3 + (size_t)n_inst, &grew)) != cudaSuccess ||
         (e = h->d_partial.ensure((size_t)P.n_parts, &grew)) != cudaSuccess ||
         (e = h->d_partial_abs.ensure((size_t)P.n_parts, &grew)) != cudaSuccess ||
         (n_groups > 0 && (e = h->d_te_all.ensure((size_t)n_inst, &grew)) != cudaSuccess))
@@ -569,6 +665,7 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
     h->last_sweep = P.var.sweep;
     h->last_pairs = P.exhaustive_pairs;
     h->last_ops = P.exhaustive_ops;
+    h->last_bundled = P.n_bundled;
     if (grew) {
         ++h->workspace_gen;
         // a fresh flag word must start cleared
@@ -581,10 +678,13 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
     uint64_t key = 1469598103934665603ull;
     key = fnv(key, P.insts.data(), P.insts.size() * sizeof(InstDesc));
     key = fnv(key, P.items.data(), P.items.size() * sizeof(WorkItem));
+    key = fnv(key, P.bitems.data(), P.bitems.size() * sizeof(WorkItem));
+    key = fnv(key, P.members.data(), P.members.size() * sizeof(int32_t));
     const void* outs[] = {te_out, err, counts, eps, te_orig, te_surr, p};
     key = fnv(key, outs, sizeof outs);
     const int cfg[] = {k, P.threads, P.grid, P.smem_floats, P.var.dlo, P.var.dhi, P.var.ks, P.var.qpt,
-                       n_groups, S, h->profiling ? 1 : 0, n_inst, P.var.sweep ? 1 : 0};
+                       n_groups, S, h->profiling ? 1 : 0, n_inst, P.var.sweep ? 1 : 0, P.bd, P.bgrid,
+                       (int)P.bsmem};
     key = fnv(key, cfg, sizeof cfg);
     const bool replay = !h->per_instance && h->graph_exec && h->graph_key == key &&
                         h->graph_gen == h->workspace_gen;
@@ -602,6 +702,8 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
         if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
             return h->cuda_fail(e, "begin capture");
         cudaError_t ce = cudaMemsetAsync(h->d_words.p, 0, sizeof(int32_t), h->cap_stream);
+        if (ce == cudaSuccess && !P.bitems.empty())
+            ce = cudaMemsetAsync(h->d_words.p + 2, 0, sizeof(int32_t), h->cap_stream);
         int launches = 0;
         if (ce == cudaSuccess && P.var.sweep) {
             ce = launch_sweep_prepass(h, P, h->cap_stream);
@@ -609,7 +711,16 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
         }
         // an event recorded during capture becomes a graph node only with cudaEventRecordExternal
         if (ce == cudaSuccess && h->profiling) ce = cudaEventRecordWithFlags(h->ev0, h->cap_stream, cudaEventRecordExternal);
-        if (ce == cudaSuccess) {
+        if (ce == cudaSuccess && !P.bitems.empty()) {
+            BatchArgs ab = a;
+            ab.items = h->d_bitems.p;
+            ab.n_items = (int)P.bitems.size();
+            ab.queue = h->d_words.p + 2;
+            ab.smem_floats = (int)(P.bsmem / sizeof(float));
+            ce = te::launch_bundle(P.bd, P.var.ks, ab, P.bgrid, P.bsmem, h->cap_stream);
+            ++launches;
+        }
+        if (ce == cudaSuccess && !P.items.empty()) {
             ce = te::launch_batched(P.var, a, P.grid, P.threads, P.smem, h->cap_stream);
             ++launches;
         }
@@ -708,6 +819,8 @@ TE_EXPORT void te_destroy(te_handle* h) {
     h->d_sidx.release();
     h->d_skey.release();
     h->d_exec.release();
+    h->d_bitems.release();
+    h->d_members.release();
     h->h_stage.release();
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
@@ -903,12 +1016,14 @@ TE_EXPORT te_status te_autotune(te_handle* h, const te_series* series, int32_t n
     DeviceGuard g(h->device);
     cudaStream_t strm = static_cast<cudaStream_t>(stream);
     const int save_t = h->cfg_threads, save_q = h->cfg_qpt;
-    const bool save_prof = h->profiling;
+    const bool save_prof = h->profiling, save_share = h->sharing;
     auto restore = [&]() {
         h->cfg_threads = save_t;
         h->cfg_qpt = save_q;
         h->profiling = save_prof;
+        h->sharing = save_share;
     };
+    h->sharing = false;  // the shapes tuned are those of the batched kernel
     h->cfg_threads = h->cfg_qpt = 0;
     Plan P;
     if ((st = build_plan(h, series, n_series, inst, n_inst, k, &P)) != TE_OK) {
@@ -1086,6 +1201,28 @@ TE_EXPORT te_status te_last_work(te_handle* h, uint64_t* pairs, uint64_t* ops, i
     if (pairs) *pairs = pr;
     if (ops) *ops = op;
     if (swept) *swept = h->last_sweep ? 1 : 0;
+    return TE_OK;
+}
+
+TE_EXPORT te_status te_set_sharing(te_handle* h, int32_t enable) {
+    if (!h) return TE_EINVAL;
+    h->sharing = enable != 0;
+    return TE_OK;
+}
+
+TE_EXPORT te_status te_last_alu_ops(te_handle* h, uint64_t* ops, int32_t* bundles) {
+    if (!h || !ops) return TE_EINVAL;
+    h->err.clear();
+    uint64_t op = h->last_ops;
+    if (h->last_sweep && h->d_exec.p) {
+        DeviceGuard g(h->device);
+        unsigned long long v[3] = {0, 0, 0};
+        cudaError_t e = cudaMemcpy(v, h->d_exec.p, sizeof v, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return h->cuda_fail(e, "read work counters");
+        op = v[1] - v[2];
+    }
+    *ops = op;
+    if (bundles) *bundles = h->last_bundled;
     return TE_OK;
 }
 

@@ -1,0 +1,378 @@
+// Target-part sharing: the estimates of one (series, window start, window, d, tau) share every
+// target coordinate of their joint points (y_t and y- of Eq. 6 / Eq. 10); they differ only in the
+// source part x-, which comes from a permuted repetition (a surrogate, Fig. 3) or another
+// interaction delay u (the scan of Eq. 5). A bundle of up to M such estimates is staged once in
+// shared memory in the order of its sort group (target part once, then each member's source
+// part), and every warp evaluates a block of 32*Q sorted queries against all members at once:
+//   pass 1: the target-part distance max(|dy_t|, |dy-|) of a (query, reference) pair is computed
+//           once and joined with each member's |dx-| to give that member's joint distance;
+//   pass 2: a = |dy_t| and b = max |dy-| are computed once and compared with each member's eps.
+// Every member's distances are exactly the ones the unshared search computes (the same FP32
+// subtractions, max is exact), so eps and the counts are identical. The key windows of the sorted
+// sweep (see te_sweep.cuh) use the largest radius over the members, a superset of each member's.
+#pragma once
+
+#include "te_sweep.cuh"
+
+namespace te {
+
+// max(a, |c_0|, ..., |c_{n-1}|) for a >= 0, three inputs per instruction
+template <int n>
+__device__ __forceinline__ float absmax_join(float a, const float (&c)[n]) {
+    float v[n + 1];
+    v[0] = a;
+#pragma unroll
+    for (int i = 0; i < n; ++i) v[i + 1] = c[i];
+    return absmax_range<0, n>(v);
+}
+
+// Stage a bundle in sorted order: columns 0..d hold the target part (y_t, y_{t'-1}, ...), columns
+// 1+d+m*d .. 1+d+m*d+d-1 member m's source part; +inf past the last point (a padded reference is
+// never inside any radius).
+template <int d, int M>
+__device__ __forceinline__ void stage_bundle(const BatchArgs& a, const InstDesc& L, const int32_t* mem, int nb,
+                                             const int32_t* __restrict__ sidx, int ldt, float* sm) {
+    constexpr int DA = 1 + d;
+    const int N = L.N;
+    const int nfill = (N + 3) & ~3;
+    for (int p = threadIdx.x; p < nfill; p += blockDim.x) {
+        if (p < N) {
+            const int i = __ldg(sidx + p);
+            const int r = i / L.W;
+            const int t = L.t_start + (i - r * L.W);
+            const float* y = L.tgt + (size_t)r * L.T;
+            sm[p] = __ldg(y + t);
+#pragma unroll
+            for (int c = 0; c < d; ++c) sm[(1 + c) * ldt + p] = __ldg(y + t - 1 - c * L.tau);
+        } else {
+#pragma unroll
+            for (int c = 0; c < DA; ++c) sm[c * ldt + p] = f_inf();
+        }
+    }
+#pragma unroll 1
+    for (int m = 0; m < nb; ++m) {
+        const InstDesc& J = a.insts[mem[m]];
+        const int32_t* perm = J.perm;
+        const float* src = J.src;
+        const int u = J.u, R = J.R;
+        float* col = sm + (DA + m * d) * ldt;
+        for (int p = threadIdx.x; p < nfill; p += blockDim.x) {
+            if (p < N) {
+                const int i = __ldg(sidx + p);
+                const int r = i / L.W;
+                const int t = L.t_start + (i - r * L.W);
+                int rs = r;
+                if (perm) {
+                    rs = __ldg(perm + r);
+                    if ((unsigned)rs >= (unsigned)R) {
+                        atomicOr(a.flags, kFlagBadPerm);
+                        rs = 0;
+                    }
+                }
+                const float* x = src + (size_t)rs * L.T;
+#pragma unroll
+                for (int c = 0; c < d; ++c) col[c * ldt + p] = __ldg(x + t - u - c * L.tau);
+            } else {
+#pragma unroll
+                for (int c = 0; c < d; ++c) col[c * ldt + p] = f_inf();
+            }
+        }
+    }
+}
+
+// Members m >= nb of a ragged bundle repeat member nb - 1 (the same staged columns and query
+// coordinates), so every loop over the members is branch-free; their results are discarded.
+template <int Q, int KS, int M>
+__device__ __forceinline__ void bundle_radii(const float (&t)[M][Q][KS], float (&r)[Q]) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        r[q] = t[0][q][KS - 1];
+#pragma unroll
+        for (int m = 1; m < M; ++m) r[q] = fmaxf(r[q], t[m][q][KS - 1]);
+    }
+}
+
+// pass 1 for one group of four references: the target part once, then every member's joint
+// distances, all of them before the first (branching) top-k insertion
+template <int d, int Q, int KS, int M>
+__device__ __forceinline__ void bknn_group(const float* __restrict__ s, const int (&coff)[M], int ldt, int j,
+                                           const u64 (&qa)[Q][1 + d], const u64 (&qc)[M][Q][d],
+                                           float (&t)[M][Q][KS]) {
+    constexpr int DA = 1 + d;
+    ulonglong2 ra[DA];
+    load_refs4<DA>(s, ldt, j, ra);
+    float ma[Q][4];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        float dx[DA], dy[DA], dz[DA], dw[DA];
+        diff4<DA>(qa[q], ra, dx, dy, dz, dw);
+        ma[q][0] = absmax_range<0, DA - 1>(dx);
+        ma[q][1] = absmax_range<0, DA - 1>(dy);
+        ma[q][2] = absmax_range<0, DA - 1>(dz);
+        ma[q][3] = absmax_range<0, DA - 1>(dw);
+    }
+    float mm[M][Q][4];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        ulonglong2 rc[d];
+        load_refs4<d>(s + coff[m], ldt, j, rc);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            float cx[d], cy[d], cz[d], cw[d];
+            diff4<d>(qc[m][q], rc, cx, cy, cz, cw);
+            mm[m][q][0] = absmax_join<d>(ma[q][0], cx);
+            mm[m][q][1] = absmax_join<d>(ma[q][1], cy);
+            mm[m][q][2] = absmax_join<d>(ma[q][2], cz);
+            mm[m][q][3] = absmax_join<d>(ma[q][3], cw);
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) topk_push(t[m][q], mm[m][q][e]);
+}
+
+// pass 1 over groups [g0, g1) in direction dir (as knn_range in te_sweep.cuh)
+template <int d, int Q, int KS, int M>
+__device__ __forceinline__ int bknn_range(const float* __restrict__ s, const int (&coff)[M], int ldt, int g0, int g1,
+                                          int dir, const u64 (&qa)[Q][1 + d], const u64 (&qc)[M][Q][d],
+                                          const float (&qkey)[Q], const bool (&qv)[Q], float (&t)[M][Q][KS]) {
+    float r[Q], lb, rb;
+    bundle_radii<Q, KS, M>(t, r);
+    warp_window(qkey, qv, r, lb, rb);
+    int n = 0;
+#pragma unroll 1
+    for (int jj = g0; jj < g1; ++jj) {
+        const int j = dir < 0 ? g1 - 1 - (jj - g0) : jj;
+        if (dir > 0 && s[ldt + 4 * j] >= rb) break;
+        if (dir < 0 && s[ldt + 4 * j + 3] <= lb) break;
+        bknn_group<d, Q, KS, M>(s, coff, ldt, j, qa, qc, t);
+        if ((++n & 3) == 0 && dir != 0) {
+            bundle_radii<Q, KS, M>(t, r);
+            warp_window(qkey, qv, r, lb, rb);
+        }
+    }
+    return n;
+}
+
+// pass 2 over groups [g0, g1) ascending inside the key window [lb, rb]
+template <int d, int Q, int M>
+__device__ __forceinline__ int bcount_range(const float* __restrict__ s, const int (&coff)[M], int ldt, int g0, int g1,
+                                            float lb, float rb, const u64 (&qa)[Q][1 + d], const u64 (&qc)[M][Q][d],
+                                            const float (&e)[M][Q], float (&cz)[M][Q], float (&cyz)[M][Q],
+                                            float (&cxz)[M][Q]) {
+    constexpr int DA = 1 + d;
+    int n = 0;
+#pragma unroll 1
+    for (int j = g0; j < g1; ++j) {
+        if (s[ldt + 4 * j] >= rb) break;
+        if (s[ldt + 4 * j + 3] <= lb) continue;
+        ulonglong2 ra[DA];
+        load_refs4<DA>(s, ldt, j, ra);
+        // a: signed dy_t (compared through |.|), b: max |dy-| (or the signed single coordinate)
+        float va[Q][4], vb[Q][4];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            float dd[4][DA];
+            diff4<DA>(qa[q], ra, dd[0], dd[1], dd[2], dd[3]);
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                va[q][x] = dd[x][0];
+                if constexpr (d == 1) vb[q][x] = dd[x][1];
+                else vb[q][x] = absmax_range<1, d>(dd[x]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            ulonglong2 rc[d];
+            load_refs4<d>(s + coff[m], ldt, j, rc);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                float cc[4][d];
+                diff4<d>(qc[m][q], rc, cc[0], cc[1], cc[2], cc[3]);
+                const float em = e[m][q];
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    float sb, sx;
+                    if constexpr (d == 1) {
+                        sb = abs_set_lt(vb[q][x], em);
+                        sx = abs_set_lt(cc[x][0], em);
+                    } else {
+                        sb = set_lt(vb[q][x], em);
+                        sx = set_lt(absmax_range<0, d - 1>(cc[x]), em);
+                    }
+                    const float sa = abs_set_lt(va[q][x], em);
+                    cz[m][q] += sb;
+                    cyz[m][q] = fmaf(sa, sb, cyz[m][q]);
+                    cxz[m][q] = fmaf(sx, sb, cxz[m][q]);
+                }
+            }
+        }
+        ++n;
+    }
+    return n;
+}
+
+// One warp's block of 32*Q sorted queries against all nb members of a staged bundle; writes one
+// partial sum per member (its part wb) and the members' optional per-point outputs.
+template <int d, int Q, int KS, int M>
+__device__ __forceinline__ void bundle_warp_block(const BatchArgs& a, const InstDesc& L, const int32_t* mem, int nb,
+                                                  const float* sm, int ldt, int wb) {
+    constexpr int DA = 1 + d;
+    constexpr int D = 1 + 2 * d;
+    const int N = L.N;
+    const int lane = threadIdx.x & 31;
+    const int32_t* sidx = a.sorted_idx + L.sort_off;
+    const int wbase = wb * 32 * Q;
+    int coff[M];  // offset of member m's source columns (ragged bundles repeat the last member)
+#pragma unroll
+    for (int m = 0; m < M; ++m) coff[m] = (DA + min(m, nb - 1) * d) * ldt;
+    u64 qa[Q][DA];
+    u64 qc[M][Q][d];
+    float qkey[Q];
+    int qidx[Q];
+    bool qv[Q];
+    int nvalid = 0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int pos = wbase + q * 32 + lane;
+        qv[q] = pos < N;
+        qidx[q] = qv[q] ? __ldg(sidx + pos) : -1;
+#pragma unroll
+        for (int c = 0; c < DA; ++c) qa[q][c] = dup2(qv[q] ? sm[c * ldt + pos] : 0.0f);
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+#pragma unroll
+            for (int c = 0; c < d; ++c)
+                qc[m][q][c] = dup2(qv[q] ? sm[coff[m] + c * ldt + pos] : 0.0f);
+        qkey[q] = qv[q] ? sm[ldt + pos] : 0.0f;
+        nvalid += __popc(__ballot_sync(0xffffffffu, qv[q]));
+    }
+    const int ng = (N + 3) >> 2;
+    unsigned long long groups_done = 0;
+
+    // ---- pass 1: own block, then right, then left (radii: largest over the members)
+    float t[M][Q][KS];
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int s = 0; s < KS; ++s) t[m][q][s] = f_inf();
+    const int g_own0 = wbase >> 2;
+    const int g_own1 = min(ng, (min(wbase + 32 * Q, N) + 3) >> 2);
+    groups_done += bknn_range<d, Q, KS, M>(sm, coff, ldt, g_own0, g_own1, 0, qa, qc, qkey, qv, t);
+    groups_done += bknn_range<d, Q, KS, M>(sm, coff, ldt, g_own1, ng, +1, qa, qc, qkey, qv, t);
+    groups_done += bknn_range<d, Q, KS, M>(sm, coff, ldt, 0, g_own0, -1, qa, qc, qkey, qv, t);
+    float e[M][Q], emax[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        emax[q] = 0.0f;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            e[m][q] = topk_select(t[m][q], a.k);
+            emax[q] = fmaxf(emax[q], e[m][q]);
+        }
+    }
+
+    // ---- pass 2: the key window of the largest eps
+    float cz[M][Q], cyz[M][Q], cxz[M][Q];
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) cz[m][q] = cyz[m][q] = cxz[m][q] = 0.0f;
+    float lb, rb;
+    warp_window(qkey, qv, emax, lb, rb);
+    const int g_lo = smem_first_greater(sm + ldt, N, lb) >> 2;
+    groups_done += bcount_range<d, Q, M>(sm, coff, ldt, g_lo, ng, lb, rb, qa, qc, e, cz, cyz, cxz);
+
+    // ---- per member: digamma terms of Eq. 9 (compensated FP32), outputs at the original index
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        if (m < nb) {
+            const InstDesc& J = a.insts[mem[m]];
+            const int64_t pt_off = J.pt_off;
+            FF acc{0.0f, 0.0f};
+            float acc_abs = 0.0f;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                if (qv[q]) {
+                    const int i = qidx[q];
+                    const int self = e[m][q] > 0.0f ? 1 : 0;
+                    const int nz = (int)cz[m][q] - self, nyz = (int)cyz[m][q] - self, nxz = (int)cxz[m][q] - self;
+                    if (a.counts_out) {
+                        int32_t* co = a.counts_out + 3 * pt_off;
+                        co[i] = nz;
+                        co[N + i] = nyz;
+                        co[2 * N + i] = nxz;
+                    }
+                    if (a.eps_out) a.eps_out[pt_off + i] = e[m][q];
+                    const float2 p1 = __ldg(a.psi + nz + 1);
+                    const float2 p2 = __ldg(a.psi + nyz + 1);
+                    const float2 p3 = __ldg(a.psi + nxz + 1);
+                    acc = ff_add(acc, p1.x, p1.y);
+                    acc = ff_add(acc, -p2.x, -p2.y);
+                    acc = ff_add(acc, -p3.x, -p3.y);
+                    acc_abs += fabsf(p1.x) + fabsf(p2.x) + fabsf(p3.x);
+                }
+            }
+            double v = (double)acc.hi + (double)acc.lo;
+            double w = (double)acc_abs;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                v += __shfl_down_sync(0xffffffffu, v, o);
+                w += __shfl_down_sync(0xffffffffu, w, o);
+            }
+            if (lane == 0) {
+                a.partial[J.part_begin + wb] = v;
+                a.partial_abs[J.part_begin + wb] = w;
+            }
+        }
+    }
+    if (a.exec && lane == 0) {
+        // pairs per member; 2 D algorithmic operations per pair; executed: the target part's
+        // 2 (1 + d) once and 2 d per member slot (M slots, padding included)
+        const unsigned long long g4 = groups_done * 4ull * (unsigned long long)nvalid;
+        const unsigned long long alg = g4 * (unsigned long long)nb * 2ull * D;
+        const unsigned long long run = g4 * (2ull * DA + (unsigned long long)M * 2ull * d);
+        atomicAdd(a.exec, g4 * (unsigned long long)nb);
+        atomicAdd(a.exec + 1, alg);
+        atomicAdd(a.exec + 2, alg > run ? alg - run : 0ull);
+    }
+}
+
+// The bundle kernel: a CTA takes a bundle (its leader's work item) from the queue, stages it,
+// and its warps take 32*Q-query blocks from a CTA-local counter.
+template <int d, int Q, int KS, int M>
+__global__ void __launch_bounds__(kBundleThreads) bundle_kernel(const BatchArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    __shared__ int s_item;
+    __shared__ int s_wblock;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int ticket = s_item;
+        if (ticket >= a.n_items) break;
+        const WorkItem w = a.items[a.item_base + ticket];
+        const InstDesc L = a.insts[w.inst];
+        const int32_t* mem = a.members + L.bundle_off;
+        const int nb = L.bundle_n;
+        const int ldt = (L.N + 3) & ~3;
+        stage_bundle<d, M>(a, L, mem, nb, a.sorted_idx + L.sort_off, ldt, sm);
+        if (threadIdx.x == 0) s_wblock = w.q0;
+        __syncthreads();
+        const int wb1 = min((L.N + 32 * Q - 1) / (32 * Q), w.q0 + L.wb_chunk);
+        for (;;) {
+            int wb = 0;
+            if ((threadIdx.x & 31) == 0) wb = atomicAdd(&s_wblock, 1);
+            wb = __shfl_sync(0xffffffffu, wb, 0);
+            if (wb >= wb1) break;
+            bundle_warp_block<d, Q, KS, M>(a, L, mem, nb, sm, ldt, wb);
+        }
+    }
+}
+
+}  // namespace te

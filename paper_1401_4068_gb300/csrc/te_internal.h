@@ -24,6 +24,8 @@ struct InstDesc {
     int32_t n_parts;
     int32_t warp_mode;     // 1: the instance is staged whole and warps take 32*Q-query blocks
     int32_t wb_chunk;      // warp mode: warp blocks per work item (an item's q0 is its first block)
+    int32_t bundle_n;      // bundle leader: members that share its target part (0: not a leader)
+    int32_t bundle_off;    // bundle leader: its members' instance indices start at members[bundle_off]
 };
 
 // Points of one (series, window start, window) group: the estimates of a group (original and
@@ -66,7 +68,9 @@ struct BatchArgs {
     float* eps_out;          // nullable: per instance [N] at pt_off
     const int32_t* sorted_idx;  // sweep mode: per group, point indices in ascending key order
     const float* sorted_key;    // sweep mode: the keys in that order
-    unsigned long long* exec;   // sweep mode: [0] evaluated (query, reference) pairs, [1] FP32 ops
+    unsigned long long* exec;   // sweep mode: [0] evaluated (query, reference) pairs, [1] their
+                                // 2 D FP32 ops, [2] ops not executed thanks to target-part sharing
+    const int32_t* members;     // bundle kernel: member instance indices (leader first)
 };
 
 // ---- launchers (te_unit.cu) ----
@@ -96,6 +100,13 @@ const void* batched_ptr_d5(int ks, int q, bool sweep);
 const void* batched_ptr_mix(int ks, int q, bool sweep);
 cudaError_t launch_batched(const BatchedVariant& v, const BatchArgs& a, int grid, int threads,
                            size_t smem, cudaStream_t s);
+
+// ---- the bundle kernel (te_bundle.cu): estimates sharing one target part, sorted sweep ----
+constexpr int kBundleMax = 4;       // members per bundle
+constexpr int kBundleQ = 1;         // queries per thread
+constexpr int kBundleThreads = 256;
+const void* bundle_kernel_ptr(int d, int ks);
+cudaError_t launch_bundle(int d, int ks, const BatchArgs& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_finalize_te(const InstDesc* insts, int n_inst, const double* partial,
                                const double* partial_abs, double psi_k, double err_coef,
                                double* te, double* err, cudaStream_t s);
