@@ -64,6 +64,7 @@ def configure(lib):
     lib.oracle_te_batch.argtypes = [P, i, P, i, i, i, P, P, P]
     lib.oracle_pvalue.argtypes = [C.c_double, P, i]
     lib.oracle_pvalue.restype = C.c_double
+    lib.oracle_points_at.argtypes = [P, i, i, i, i, P, i, i, P, P]
     return lib
 
 
@@ -125,6 +126,21 @@ def range_count(points: np.ndarray, dy: int, dx: int, eps: np.ndarray) -> np.nda
     out = np.empty((3, N), dtype=np.int32)
     _check(lib.oracle_range_count(_ptr(pts), N, dy, dx, _ptr(e), _ptr(out)), "range_count")
     return out
+
+
+def points_at(points: np.ndarray, dy: int, dx: int, k: int, idx, n_threads: Optional[int] = None):
+    """(eps[n], counts[3][n]) of the query points ``idx`` only (same definitions as knn and
+    range_count), for point sets too large to evaluate whole."""
+    lib = _load()
+    pts = np.ascontiguousarray(points, dtype=np.float32)
+    N = pts.shape[0]
+    assert pts.shape[1] == 1 + dy + dx
+    ix = np.ascontiguousarray(idx, dtype=np.int32)
+    eps = np.empty(len(ix), dtype=np.float32)
+    out = np.empty((3, len(ix)), dtype=np.int32)
+    _check(lib.oracle_points_at(_ptr(pts), N, dy, dx, k, _ptr(ix), len(ix), n_threads or default_threads(),
+                                _ptr(eps), _ptr(out)), "points_at")
+    return eps, out
 
 
 def digamma(n: int) -> float:

@@ -103,25 +103,29 @@ static int cmp_nb(const void* pa, const void* pb)
 
 /* ------------------------------------------------------------------------------------------
  * kNN in the joint space: eps_i = k-th smallest of { dist(i, j) : j != i }
+ * (a: scratch for the N-1 distances of point i)
  * ---------------------------------------------------------------------------------------- */
+static void knn_point(const float* points, int N, int D, int k, int i, nb_t* a, float* eps_i, int32_t* nn_i)
+{
+    int n = 0;
+    for (int j = 0; j < N; ++j) {
+        if (j == i) continue;
+        a[n].dist = maxnorm(points + (size_t)i * D, points + (size_t)j * D, 0, D);
+        a[n].j = j;
+        ++n;
+    }
+    qsort(a, (size_t)n, sizeof(nb_t), cmp_nb);
+    *eps_i = a[k - 1].dist;
+    if (nn_i)
+        for (int m = 0; m < k; ++m) nn_i[m] = a[m].j;
+}
+
 int oracle_knn(const float* points, int N, int D, int k, float* eps, int32_t* nn)
 {
     if (!points || !eps || D < 1 || k < 1 || N < k + 1) return 1;
     nb_t* a = (nb_t*)malloc((size_t)(N - 1) * sizeof(nb_t));
     if (!a) return 3;
-    for (int i = 0; i < N; ++i) {
-        int n = 0;
-        for (int j = 0; j < N; ++j) {
-            if (j == i) continue;
-            a[n].dist = maxnorm(points + (size_t)i * D, points + (size_t)j * D, 0, D);
-            a[n].j = j;
-            ++n;
-        }
-        qsort(a, (size_t)n, sizeof(nb_t), cmp_nb);
-        eps[i] = a[k - 1].dist;
-        if (nn)
-            for (int m = 0; m < k; ++m) nn[(size_t)i * k + m] = a[m].j;
-    }
+    for (int i = 0; i < N; ++i) knn_point(points, N, D, k, i, a, eps + i, nn ? nn + (size_t)i * k : NULL);
     free(a);
     return 0;
 }
@@ -132,27 +136,83 @@ int oracle_knn(const float* points, int N, int D, int k, float* eps, int32_t* nn
  *   n_yz : points with max-norm distance < eps in the (y_t, y-) space (coords 0 .. dy)
  *   n_xz : points with max-norm distance < eps in the (y-, x-) space  (coords 1 .. dy+dx)
  * ---------------------------------------------------------------------------------------- */
+static void count_point(const float* points, int N, int dy, int dx, int i, float e, int32_t* nz_i,
+                        int32_t* nyz_i, int32_t* nxz_i)
+{
+    const int D = 1 + dy + dx;
+    const float* pi = points + (size_t)i * D;
+    int32_t nz = 0, nyz = 0, nxz = 0;
+    for (int j = 0; j < N; ++j) {
+        if (j == i) continue;
+        const float* pj = points + (size_t)j * D;
+        if (maxnorm(pi, pj, 1, 1 + dy) < e) ++nz;
+        if (maxnorm(pi, pj, 0, 1 + dy) < e) ++nyz;
+        if (maxnorm(pi, pj, 1, D) < e) ++nxz;
+    }
+    *nz_i = nz;
+    *nyz_i = nyz;
+    *nxz_i = nxz;
+}
+
 int oracle_range_count(const float* points, int N, int dy, int dx, const float* eps,
                        int32_t* counts)
 {
     if (!points || !eps || !counts || N < 1 || dy < 0 || dx < 0) return 1;
-    const int D = 1 + dy + dx;
-    for (int i = 0; i < N; ++i) {
-        const float* pi = points + (size_t)i * D;
-        const float e = eps[i];
-        int32_t nz = 0, nyz = 0, nxz = 0;
-        for (int j = 0; j < N; ++j) {
-            if (j == i) continue;
-            const float* pj = points + (size_t)j * D;
-            if (maxnorm(pi, pj, 1, 1 + dy) < e) ++nz;
-            if (maxnorm(pi, pj, 0, 1 + dy) < e) ++nyz;
-            if (maxnorm(pi, pj, 1, D) < e) ++nxz;
-        }
-        counts[i] = nz;
-        counts[(size_t)N + i] = nyz;
-        counts[(size_t)2 * N + i] = nxz;
-    }
+    for (int i = 0; i < N; ++i)
+        count_point(points, N, dy, dx, i, eps[i], counts + i, counts + (size_t)N + i, counts + (size_t)2 * N + i);
     return 0;
+}
+
+/* eps and the three counts of selected query points only (the same per-point definitions as
+ * oracle_knn / oracle_range_count), host threads split the points: for checking outputs of
+ * point sets too large to evaluate whole. counts is [3][n_idx]. */
+typedef struct {
+    const float* points;
+    int N, dy, dx, k, n_idx, tid, nthreads, rc;
+    const int32_t* idx;
+    float* eps;
+    int32_t* counts;
+} at_job;
+
+static void* at_worker(void* arg)
+{
+    at_job* jb = (at_job*)arg;
+    const int D = 1 + jb->dy + jb->dx;
+    nb_t* a = (nb_t*)malloc((size_t)(jb->N - 1) * sizeof(nb_t));
+    if (!a) {
+        jb->rc = 3;
+        return NULL;
+    }
+    for (int q = jb->tid; q < jb->n_idx; q += jb->nthreads) {
+        const int i = jb->idx[q];
+        knn_point(jb->points, jb->N, D, jb->k, i, a, jb->eps + q, NULL);
+        count_point(jb->points, jb->N, jb->dy, jb->dx, i, jb->eps[q], jb->counts + q,
+                    jb->counts + (size_t)jb->n_idx + q, jb->counts + (size_t)2 * jb->n_idx + q);
+    }
+    free(a);
+    return NULL;
+}
+
+int oracle_points_at(const float* points, int N, int dy, int dx, int k, const int32_t* idx, int n_idx,
+                     int n_threads, float* eps, int32_t* counts)
+{
+    if (!points || !idx || !eps || !counts || N < k + 1 || k < 1 || dy < 0 || dx < 0 || n_idx < 0) return 1;
+    for (int q = 0; q < n_idx; ++q)
+        if (idx[q] < 0 || idx[q] >= N) return 1;
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > 256) n_threads = 256;
+    pthread_t th[256];
+    at_job jobs[256];
+    for (int t = 0; t < n_threads; ++t) {
+        jobs[t] = (at_job){points, N, dy, dx, k, n_idx, t, n_threads, 0, idx, eps, counts};
+        pthread_create(&th[t], NULL, at_worker, &jobs[t]);
+    }
+    int rc = 0;
+    for (int t = 0; t < n_threads; ++t) {
+        pthread_join(th[t], NULL);
+        if (jobs[t].rc) rc = jobs[t].rc;
+    }
+    return rc;
 }
 
 /* ------------------------------------------------------------------------------------------

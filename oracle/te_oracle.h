@@ -40,6 +40,11 @@ int oracle_knn(const float* points, int N, int D, int k, float* eps, int32_t* nn
 int oracle_range_count(const float* points, int N, int dy, int dx, const float* eps,
                        int32_t* counts);
 
+/* eps and counts ([3][n_idx]: n_z, n_yz, n_xz) of the query points idx[0..n_idx-1] only, by the
+ * same per-point definitions as oracle_knn / oracle_range_count; host threads split the points. */
+int oracle_points_at(const float* points, int N, int dy, int dx, int k, const int32_t* idx, int n_idx,
+                     int n_threads, float* eps, int32_t* counts);
+
 /* Digamma at a positive integer, FP64, from psi(1) = -gamma and psi(n+1) = psi(n) + 1/n. */
 double oracle_digamma(int n);
 

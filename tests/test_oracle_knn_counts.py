@@ -140,3 +140,17 @@ def test_invalid_sizes():
     pts = _rand_points(4, 1, 1, 6)
     with pytest.raises(ValueError):
         oracle.knn(pts, 4)
+
+
+def test_points_at_equals_the_whole_set_evaluation():
+    """The sampled-query entry (used on point sets too large to evaluate whole) gives exactly
+    the radii and counts of the full evaluation at the chosen points, ties included."""
+    rng = np.random.default_rng(12)
+    for pts, dy, dx in ((rng.standard_normal((400, 7)).astype(np.float32), 3, 3),
+                        (rng.integers(0, 3, (150, 5)).astype(np.float32), 2, 2)):
+        eps = oracle.knn(pts, 4)
+        c = oracle.range_count(pts, dy, dx, eps)
+        idx = [0, 1, 77, len(pts) - 1, 42]
+        e2, c2 = oracle.points_at(pts, dy, dx, 4, idx)
+        np.testing.assert_array_equal(e2, eps[idx])
+        np.testing.assert_array_equal(c2, c[:, idx])

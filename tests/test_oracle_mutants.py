@@ -24,9 +24,9 @@ MUTANTS = [
     ("non-strict count", "< e) ++nz", "<= e) ++nz"),
     ("wrong digamma sign", "- psi[c[(size_t)N + i] + 1]", "+ psi[c[(size_t)N + i] + 1]"),
     ("dropped digamma term", " - psi[c[(size_t)2 * N + i] + 1]", ""),
-    ("eps off by one", "eps[i] = a[k - 1].dist", "eps[i] = a[k > 1 ? k - 2 : 0].dist"),
-    ("self counted in the range counts", "            if (j == i) continue;\n            const float* pj",
-     "            const float* pj"),
+    ("eps off by one", "*eps_i = a[k - 1].dist", "*eps_i = a[k > 1 ? k - 2 : 0].dist"),
+    ("self counted in the range counts", "        if (j == i) continue;\n        const float* pj",
+     "        const float* pj"),
     ("target past index", "y[t - 1 - m * tau]", "y[t - m * tau]"),
     ("source delay index", "x[t - u - m * tau]", "x[t - u + 1 - m * tau]"),
     ("digamma recurrence", "t[n + 1] = t[n] + 1.0 / (double)n", "t[n + 1] = t[n] + 1.0 / (double)(n + 1)"),
