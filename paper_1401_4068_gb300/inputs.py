@@ -342,6 +342,132 @@ def ar1_analysis(name: str = "unidirectional", S: int = 500, R: int = 50, window
                     extra=dict(u_lo=1, u_hi=u_hi))
 
 
+# ---------------------------------------------------------------------------------------
+# Two unidirectionally coupled Lorenz systems X -> Y (Eq. 11): for system i in {X, Y}
+#   dU_i/dt = sigma (V_i - U_i)
+#   dV_i/dt = U_i (rho_i - W_i) - V_i + gamma_XY(t) V_X(t - delta)^2   (the last term for i = Y only)
+#   dW_i/dt = U_i V_i - beta W_i
+# The paper analyses the V coordinates and states gamma_XY = 0.3, delta = 45 ms, 1 kHz sampling,
+# but not sigma, rho, beta, the solver's time scale or the initial states: those below are this
+# implementation's choices (classic Lorenz constants; one sample = 0.01 model time units, so the
+# coupling delay is 0.45 units = 45 samples; random initial states relaxed for 1000 samples).
+LORENZ_SIGMA = 10.0
+LORENZ_BETA = 8.0 / 3.0
+LORENZ_RHO = (28.0, 28.0)      # rho_X, rho_Y
+LORENZ_DT = 0.01               # model time units per sample
+LORENZ_SUBSTEPS = 4            # fourth-order Runge-Kutta steps per sample
+LORENZ_DELAY = 45              # delta_XY in samples
+LORENZ_GAMMA = 0.3
+LORENZ_BURN = 1000
+
+
+def lorenz_pair(rng: np.random.Generator, R: int, T: int, gamma: float = LORENZ_GAMMA,
+                delay: int = LORENZ_DELAY, coupled=(1000, 2000), burn: int = LORENZ_BURN,
+                substeps: int = LORENZ_SUBSTEPS):
+    """R repetitions of T samples of the Eq. 11 pair; returns (src = V_X, tgt = V_Y) float32.
+
+    ``coupled``: kept-sample interval [a, b) in which gamma_XY = gamma (None: all samples,
+    burn-in included); gamma_XY = 0 elsewhere.  The delay-differential equation is integrated
+    with classical RK4 on a grid of ``substeps`` steps per sample; the delayed V_X at a step's
+    midpoint is the mean of the two neighbouring grid values (linear interpolation), and before
+    the first ``delay`` samples the history is the initial state (a constant initial function).
+    """
+    h = LORENZ_DT / substeps
+    lag = delay * substeps                      # delay in grid steps
+    rho = np.array(LORENZ_RHO).reshape(2, 1)
+    u = rng.uniform(-15.0, 15.0, (2, R))
+    v = rng.uniform(-15.0, 15.0, (2, R))
+    w = rng.uniform(5.0, 40.0, (2, R))
+    hist = np.repeat(v[0][None, :], lag + 1, axis=0)   # V_X on the last lag + 1 grid points
+    out = np.empty((2, R, T), dtype=np.float32)
+
+    def f(u, v, w, c):
+        du = LORENZ_SIGMA * (v - u)
+        dv = u * (rho - w) - v
+        dv[1] += c
+        dw = u * v - LORENZ_BETA * w
+        return du, dv, dw
+
+    n_steps = (burn + T) * substeps
+    for n in range(n_steps):
+        sample = n // substeps - burn               # kept-sample index of this step
+        if n % substeps == 0 and sample >= 0:
+            out[:, :, sample] = v
+        hist[n % (lag + 1)] = v[0]
+        on = (coupled is None) or (coupled[0] <= sample < coupled[1])
+        g = gamma if on else 0.0
+        if g != 0.0:
+            x0 = hist[(n + 1) % (lag + 1)]          # V_X(t_n - delta)
+            x1 = hist[(n + 2) % (lag + 1)] if lag >= 1 else v[0]   # V_X(t_n + h - delta)
+            c0, ch, c1 = g * x0 * x0, g * (0.5 * (x0 + x1)) ** 2, g * x1 * x1
+        else:
+            c0 = ch = c1 = 0.0
+        k1 = f(u, v, w, c0)
+        k2 = f(u + 0.5 * h * k1[0], v + 0.5 * h * k1[1], w + 0.5 * h * k1[2], ch)
+        k3 = f(u + 0.5 * h * k2[0], v + 0.5 * h * k2[1], w + 0.5 * h * k2[2], ch)
+        k4 = f(u + h * k3[0], v + h * k3[1], w + h * k3[2], c1)
+        u = u + h / 6.0 * (k1[0] + 2.0 * k2[0] + 2.0 * k3[0] + k4[0])
+        v = v + h / 6.0 * (k1[1] + 2.0 * k2[1] + 2.0 * k3[1] + k4[1])
+        w = w + h / 6.0 * (k1[2] + 2.0 * k2[2] + 2.0 * k3[2] + k4[2])
+    return np.ascontiguousarray(out[0]), np.ascontiguousarray(out[1])
+
+
+# Embedding of the Lorenz V coordinates (the paper uses "optimal" parameters without stating
+# them; its benchmark chunk has 17 = 1 + 2 * 8 joint coordinates, so d = 8 there).
+LORENZ_D = 3
+LORENZ_TAU = 8
+
+
+def lorenz_analysis(S: int = 500, R: int = 150, T: int = 3000, d: int = LORENZ_D, tau: int = LORENZ_TAU,
+                    seed: int = 0) -> Workload:
+    """The paper's non-stationary Lorenz analysis (Fig. 6): 150 repetitions x 3000 samples, coupling
+    gamma_XY = 0.3 with delay 45 samples during samples 1000..2000 only, analysis windows
+    200..450, 1600..1850 and 2750..3000 (250 samples), delays scanned over 35..55, S surrogates,
+    k = 4.  The instances hold the original and surrogates at the true delay; a delay scan
+    supplies u."""
+    rng = np.random.default_rng(BASE_SEED + 80 + seed)
+    src, tgt = lorenz_pair(rng, R, T)
+    perms = permutations(rng, S, R)
+    s = Series(src, tgt, d=d, tau=tau, u=LORENZ_DELAY, perms=perms)
+    ts = [t for t in (200, 1600, 2750) if t + 250 <= T]
+    return Workload(f"Lorenz X->Y (Eq. 11), {R} repetitions, windows of 250", [s],
+                    _surrogate_instances([ts], 250, S), k=4, t_starts=[ts], window=250, S=S,
+                    extra=dict(u_lo=35, u_hi=55))
+
+
+def lorenz_robustness(S: int = 100, R: int = 300, d: int = LORENZ_D, tau: int = LORENZ_TAU,
+                      trials=(3, 10, 25, 50, 150), seed: int = 0):
+    """The robustness analysis (Fig. 8): coupled Lorenz systems (gamma_XY = 0.3 throughout, delay
+    45 samples), repetitions of 300 samples, delays scanned over 30..60.  The paper takes the
+    first M = 500 .. 30000 embedded points; here a point set is the first R_M whole repetitions
+    over the window 100..299 (200 points each): M = 600, 2000, 5000, 10000, 30000.
+    Returns {M: Workload} (one series per M, the first R_M repetitions, S surrogates each)."""
+    rng = np.random.default_rng(BASE_SEED + 90 + seed)
+    src, tgt = lorenz_pair(rng, R, 300, coupled=None)
+    out = {}
+    for r_m in trials:
+        perms = permutations(rng, S, r_m)
+        s = Series(np.ascontiguousarray(src[:r_m]), np.ascontiguousarray(tgt[:r_m]), d=d, tau=tau,
+                   u=LORENZ_DELAY, perms=perms)
+        out[r_m * 200] = Workload(f"Lorenz robustness, M = {r_m * 200} points", [s],
+                                  _surrogate_instances([[100]], 200, S), k=4, t_starts=[[100]],
+                                  window=200, S=S, extra=dict(u_lo=30, u_hi=60))
+    return out
+
+
+def paper_chunk(chunks: int = 16, seed: int = 0) -> Workload:
+    """The benchmark chunk of the paper's performance test: 30094 points in the 17-D joint space
+    (d = 8) of coupled Lorenz data, k = 4.  Here 82 repetitions x a window of 367 samples
+    (t' = 133..499, u = 45, tau = 1); ``chunks`` estimates of that shape (the original pairing
+    and chunks - 1 trial-shuffled surrogates: same shape and cost, different point sets)."""
+    rng = np.random.default_rng(BASE_SEED + 95 + seed)
+    src, tgt = lorenz_pair(rng, 82, 500, coupled=None)
+    perms = permutations(rng, max(1, chunks - 1), 82)
+    s = Series(src, tgt, d=8, tau=1, u=LORENZ_DELAY, perms=perms)
+    insts = [Instance(0, 133, 367, -1)] + [Instance(0, 133, 367, c) for c in range(chunks - 1)]
+    return Workload("paper benchmark chunk: 30094 points x 17-D (d = 8), Lorenz", [s], insts, k=4)
+
+
 def sample_instances(w: Workload, n: int, seed: int = 0) -> List[int]:
     """Indices of a seeded, cost-stratified subset of a workload's instances."""
     rng = np.random.default_rng(BASE_SEED + 1000 + seed)

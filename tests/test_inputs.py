@@ -59,3 +59,60 @@ def test_ar1_scenario_shapes():
     assert x.shape == (4, 500) and y.dtype == np.float32
     w = I.ar1_analysis("unidirectional", S=3, R=5)
     assert w.t_starts[0] == [200, 500, 800, 1100] and w.window == 300
+
+
+# ---- coupled Lorenz systems (Eq. 11)
+def test_lorenz_attractor_statistics():
+    """Uncoupled, each system is the classic Lorenz attractor (sigma 10, rho 28, beta 8/3), whose
+    y coordinate (V here) has mean 0 by symmetry and a standard deviation of about 9.0."""
+    rng = np.random.default_rng(3)
+    x, y = I.lorenz_pair(rng, 40, 3000, gamma=0.0)
+    for v in (x, y):
+        assert np.isfinite(v).all()
+        assert abs(float(v.mean())) < 0.6
+        assert 8.6 < float(v.std()) < 9.4
+
+
+def test_lorenz_coupling_is_unidirectional_and_windowed():
+    """X never depends on Y; Y is unchanged before the coupling interval and changed inside it."""
+    a = I.lorenz_pair(np.random.default_rng(4), 6, 1500, coupled=(1000, 2000))
+    b = I.lorenz_pair(np.random.default_rng(4), 6, 1500, gamma=0.0)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1][:, :1000], b[1][:, :1000])
+    assert np.abs(a[1][:, 1100:] - b[1][:, 1100:]).max() > 1.0
+
+
+def test_lorenz_coupling_delay():
+    """V_X(t - delta)^2 drives dV_Y/dt: its correlation with the increments of V_Y peaks near the
+    coupling delay (45 samples) and is small far from it."""
+    x, y = I.lorenz_pair(np.random.default_rng(5), 40, 1200, coupled=None)
+    dy = np.diff(y.astype(np.float64), axis=1)
+    corr = {}
+    for lag in range(20, 71, 2):
+        xs = x[:, 200 - lag:1100 - lag].astype(np.float64) ** 2
+        corr[lag] = np.corrcoef(xs.ravel(), dy[:, 200:1100].ravel())[0, 1]
+    best = max(corr, key=corr.get)
+    assert 38 <= best <= 46, corr
+    assert corr[best] > 0.3 and corr[20] < 0.2
+
+
+def test_lorenz_integrator_converges():
+    """Over a short horizon the RK4 solution with 4 steps per sample agrees with 16 steps per
+    sample to well below the signal scale (fourth-order method, smooth solution)."""
+    a = I.lorenz_pair(np.random.default_rng(6), 4, 60, burn=0, substeps=4, coupled=None)
+    b = I.lorenz_pair(np.random.default_rng(6), 4, 60, burn=0, substeps=16, coupled=None)
+    assert np.abs(a[1] - b[1]).max() < 2e-3
+    assert np.abs(a[0] - b[0]).max() < 2e-3
+
+
+def test_lorenz_workload_shapes():
+    w = I.lorenz_analysis(S=3, R=8, T=3000)
+    assert w.t_starts == [[200, 1600, 2750]] and w.window == 250
+    assert (w.extra["u_lo"], w.extra["u_hi"]) == (35, 55)
+    assert len(w.instances) == 3 * 4 and w.n_points(w.instances[0]) == 8 * 250
+    rob = I.lorenz_robustness(S=2, R=12, trials=(3, 10))
+    assert sorted(rob) == [600, 2000]
+    assert rob[2000].n_points(rob[2000].instances[0]) == 2000
+    c = I.paper_chunk(chunks=3)
+    assert len(c.instances) == 3
+    assert c.n_points(c.instances[0]) == 30094 and c.joint_dim(c.instances[0]) == 17
