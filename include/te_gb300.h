@@ -47,7 +47,7 @@ typedef enum te_status {
 } te_status;
 
 /* Embedding parameters of one estimate (paper notation):
- *   d       embedding dimension of target and source past states (Eq. 6 / Eq. 7): 1 <= d <= 5
+ *   d       embedding dimension of target and source past states (Eq. 6 / Eq. 7): 1 <= d <= 8
  *           for te_estimate / te_surrogate_test, 1 <= d <= 15 for te_embed
  *   tau     embedding delay in samples (Eq. 6), tau >= 1
  *   u       assumed interaction delay: the source state is taken at t - u (Eq. 3), u >= 0
@@ -143,7 +143,8 @@ te_status te_range_count(te_handle* h, const float* points, int32_t N, int32_t d
  *            the same counts| from that summation.
  *   counts   device int32 or NULL: per instance its [3][N_i] block, blocks concatenated in
  *            instance order.   eps: device float32 or NULL: per instance [N_i], concatenated.
- * Limits: N_i <= 65536, 1 <= d <= 5, k <= 16 (TE_ENOTIMPL beyond). */
+ * Limits: N_i <= 65536, 1 <= d <= 8, k <= 16; a batch that mixes embedding dimensions has
+ * d <= 5 (TE_ENOTIMPL beyond). */
 te_status te_estimate(te_handle* h, const te_series* series, int32_t n_series,
                       const te_instance* inst, int32_t n_inst, int32_t k, double* te,
                       double* err_bound, int32_t* counts, float* eps, void* stream);
@@ -206,7 +207,7 @@ te_status te_autotune(te_handle* h, const te_series* series, int32_t n_series, c
  *      and each warp visits only references whose key lies inside the window its queries' radii
  *      allow: every distance the estimator compares is at least fl(|key_q - key_j|), and the window
  *      bounds are rounded outward, so no reference that could enter a top-k list or a count is
- *      skipped. Used when every point count is <= 16384 (otherwise the exhaustive search runs).
+ *      skipped. Applies to every point count (up to the 65536 limit of an estimate).
  *   0: exhaustive search over all N^2 pairs (the paper's brute force, Implementation section). */
 te_status te_set_search(te_handle* h, int32_t mode);
 

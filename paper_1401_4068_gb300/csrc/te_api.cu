@@ -27,7 +27,9 @@ constexpr int kMaxN = 65536;          // largest point count of one estimate
 constexpr int kMaxK = 16;
 constexpr int kMaxD = 32;             // te_knn_maxnorm / te_range_count
 constexpr int kMaxEmbedDim = 15;      // te_embed: D = 1 + 2d <= 31
-constexpr int kMaxBatchedD = 5;       // te_estimate / te_surrogate_test
+constexpr int kMaxBatchedD = 8;       // te_estimate / te_surrogate_test / te_delay_scan
+constexpr int kMaxMixedD = 5;         // largest d of a batch that mixes embedding dimensions
+constexpr int kMaxBundleD = 5;        // target-part sharing
 constexpr int kSmemCapBytes = 64 * 1024;  // reference tile budget of the batched kernel
 constexpr int kSweepSmemMaxBytes = 160 * 1024;  // sweep mode: room for whole query blocks per tile
 constexpr int64_t kResidentMaxBytes = 200 * 1024;  // sweep mode: whole instances in shared memory
@@ -164,8 +166,8 @@ struct te_handle {
     DevBuf<double> d_partial, d_partial_abs, d_te_all, d_surr_ws, d_p_ws;
     DevBuf<float2> d_psi;
     DevBuf<te::SortGroup> d_groups;
-    DevBuf<int32_t> d_sidx;
-    DevBuf<float> d_skey;
+    DevBuf<int32_t> d_sidx, d_sidx_tmp;
+    DevBuf<float> d_skey, d_skey_tmp;
     DevBuf<unsigned long long> d_exec;
     DevBuf<WorkItem> d_bitems;
     DevBuf<int32_t> d_members;
@@ -271,9 +273,11 @@ std::string shape_signature(const std::vector<InstDesc>& insts, int ks) {
 void choose_shape(te_handle* h, const std::vector<InstDesc>& insts, int ks, int* threads, int* qpt) {
     int dmax = 1;
     for (const auto& I : insts) dmax = std::max(dmax, I.d);
-    // the sweep prefers 2 (narrower key windows per warp, no register spills)
+    // the sweep prefers 2 (narrower key windows per warp, no register spills); d >= 6 runs one
+    // query per thread
     int q = (ks == 5 && dmax <= 4 && h->search_mode == 0) ? 4 : 2;
     if (h->cfg_qpt) q = ks == 5 ? h->cfg_qpt : 2;
+    if (dmax > 5) q = 1;
     *qpt = q;
     if (h->cfg_threads) {
         *threads = h->cfg_threads;
@@ -348,6 +352,9 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
         dmaxN = std::max(dmaxN, (int)(((N + 3) & ~3) * (1 + 2 * S.d)));
     }
     P->n_points = off;
+    if (dlo != dhi && dhi > kMaxMixedD)
+        return h->fail(TE_ENOTIMPL, "a batch that mixes embedding dimensions must have d <= %d (got %d..%d)",
+                       kMaxMixedD, dlo, dhi);
     const int ks = k <= 4 ? 5 : 17;
     int threads, qpt;
     choose_shape(h, P->insts, ks, &threads, &qpt);
@@ -414,7 +421,7 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
                 const int64_t bytes = (int64_t)((I.N + 3) & ~3) * (1 + I.d + te::kBundleMax * I.d) * 4;
                 if (bytes <= kResidentMaxBytes) shareable[I.d] += (int64_t)kv.second.size();
             }
-        for (int d = 1; d <= kMaxBatchedD; ++d)
+        for (int d = 1; d <= kMaxBundleD; ++d)
             if (shareable[d] > (P->bd ? shareable[P->bd] : 0)) P->bd = d;
         int n_bundles = 0;
         for (const auto& kv : by_target) {
@@ -564,6 +571,10 @@ te_status prepare_sweep(te_handle* h, const Plan& P, bool* grew) {
         (e = h->d_bitems.ensure(P.bitems.size(), grew)) != cudaSuccess ||
         (e = h->d_members.ensure(P.members.size(), grew)) != cudaSuccess)
         return h->fail(TE_ENOMEM, "sweep workspace: %s", cudaGetErrorString(e));
+    if (te::sort_needs_scratch(P.nmax) &&
+        ((e = h->d_sidx_tmp.ensure((size_t)P.sorted_total, grew)) != cudaSuccess ||
+         (e = h->d_skey_tmp.ensure((size_t)P.sorted_total, grew)) != cudaSuccess))
+        return h->fail(TE_ENOMEM, "sort scratch: %s", cudaGetErrorString(e));
     if ((e = te::prepare_sort_kernel(P.nmax)) != cudaSuccess) return h->cuda_fail(e, "sort kernel attribute");
     return TE_OK;
 }
@@ -573,7 +584,8 @@ cudaError_t launch_sweep_prepass(te_handle* h, const Plan& P, cudaStream_t s) {
     if (!P.var.sweep) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(h->d_exec.p, 0, 3 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    return te::launch_sort_groups(h->d_groups.p, (int)P.groups.size(), P.nmax, h->d_sidx.p, h->d_skey.p, s);
+    return te::launch_sort_groups(h->d_groups.p, (int)P.groups.size(), P.nmax, h->d_sidx.p, h->d_skey.p,
+                                  h->d_sidx_tmp.p, h->d_skey_tmp.p, s);
 }
 
 BatchArgs batch_args(te_handle* h, const Plan& P, int k, int32_t* counts, float* eps) {
@@ -818,6 +830,8 @@ TE_EXPORT void te_destroy(te_handle* h) {
     h->d_groups.release();
     h->d_sidx.release();
     h->d_skey.release();
+    h->d_sidx_tmp.release();
+    h->d_skey_tmp.release();
     h->d_exec.release();
     h->d_bitems.release();
     h->d_members.release();
@@ -1049,7 +1063,8 @@ TE_EXPORT te_status te_autotune(te_handle* h, const te_series* series, int32_t n
         for (int i = 0; i < n_inst; i += stride) sub.push_back(inst[order[i]]);
         int dmax = 1;
         for (const auto& I : P.insts) dmax = std::max(dmax, I.d);
-        std::vector<int> qs = (ks == 5 && dmax <= 4) ? std::vector<int>{4, 2} : std::vector<int>{2};
+        std::vector<int> qs = dmax > 5 ? std::vector<int>{1}
+                              : (ks == 5 && dmax <= 4) ? std::vector<int>{4, 2} : std::vector<int>{2};
         bool uniform = true;
         for (const auto& I : P.insts) uniform &= I.N == P.insts[0].N;
         bool grew = false;

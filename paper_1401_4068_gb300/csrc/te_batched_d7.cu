@@ -1,0 +1,6 @@
+// Instantiations of the persistent batched kernel for embedding dimension d = 7.
+#include "te_kernels.cuh"
+
+namespace te {
+TE_BATCHED_PTR_FN_WIDE(batched_ptr_d7, 7)
+}  // namespace te

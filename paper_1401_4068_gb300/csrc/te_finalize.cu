@@ -84,10 +84,13 @@ const void* batched_kernel_ptr(const BatchedVariant& v) {
             case 3: return batched_ptr_d3(v.ks, v.qpt, v.sweep);
             case 4: return batched_ptr_d4(v.ks, v.qpt, v.sweep);
             case 5: return batched_ptr_d5(v.ks, v.qpt, v.sweep);
+            case 6: return batched_ptr_d6(v.ks, v.qpt, v.sweep);
+            case 7: return batched_ptr_d7(v.ks, v.qpt, v.sweep);
+            case 8: return batched_ptr_d8(v.ks, v.qpt, v.sweep);
             default: return nullptr;
         }
     }
-    return batched_ptr_mix(v.ks, v.qpt, v.sweep);
+    return v.dhi <= 5 ? batched_ptr_mix(v.ks, v.qpt, v.sweep) : nullptr;
 }
 
 cudaError_t launch_batched(const BatchedVariant& v, const BatchArgs& a, int grid, int threads,

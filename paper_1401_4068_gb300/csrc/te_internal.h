@@ -37,8 +37,9 @@ struct SortGroup {
     int64_t off;           // offset of the group's sorted index / key arrays
 };
 
-// Largest point count the sweep mode sorts (in shared memory, one CTA per group).
-constexpr int kSweepMaxN = 16384;
+// Largest point count the sweep mode sorts (one CTA per group; runs in shared memory, merges
+// through global memory above 8192 points).
+constexpr int kSweepMaxN = 65536;
 
 // One unit of work of the persistent kernel: queries q0 .. q0 + threads*qpt - 1 of an instance.
 struct WorkItem {
@@ -83,13 +84,15 @@ cudaError_t launch_count(const float* pts, int N, int dy, int dx, int ld, const 
                          int32_t* counts, int sm_count, cudaStream_t s);
 
 // ---- launchers (te_batched_*.cu, te_finalize.cu) ----
-// Variant of the persistent kernel: d in [dlo, dhi] (dlo == dhi: specialised), ks = k-slots.
+// Variant of the persistent kernel: d in [dlo, dhi] (dlo == dhi: specialised, d = 1..8; else
+// dhi <= 5), ks = k-slots, qpt = queries per thread (1 for d >= 6).
 struct BatchedVariant {
     int dlo, dhi, ks, qpt;
     bool sweep;  // sorted-sweep search instead of the exhaustive one
 };
 cudaError_t launch_sort_groups(const SortGroup* groups, int n_groups, int nmax, int32_t* idx, float* key,
-                               cudaStream_t s);
+                               int32_t* tmp_idx, float* tmp_key, cudaStream_t s);
+bool sort_needs_scratch(int nmax);  // tmp_idx / tmp_key (sorted_total entries) are used
 cudaError_t prepare_sort_kernel(int nmax);
 const void* batched_kernel_ptr(const BatchedVariant& v);
 const void* batched_ptr_d1(int ks, int q, bool sweep);
@@ -97,6 +100,9 @@ const void* batched_ptr_d2(int ks, int q, bool sweep);
 const void* batched_ptr_d3(int ks, int q, bool sweep);
 const void* batched_ptr_d4(int ks, int q, bool sweep);
 const void* batched_ptr_d5(int ks, int q, bool sweep);
+const void* batched_ptr_d6(int ks, int q, bool sweep);
+const void* batched_ptr_d7(int ks, int q, bool sweep);
+const void* batched_ptr_d8(int ks, int q, bool sweep);
 const void* batched_ptr_mix(int ks, int q, bool sweep);
 cudaError_t launch_batched(const BatchedVariant& v, const BatchArgs& a, int grid, int threads,
                            size_t smem, cudaStream_t s);

@@ -1,7 +1,7 @@
 // The persistent batched kernel: a CTA takes (instance, query tile) work items from a device queue
 // (atomic ticket, no waits) and runs the exhaustive search (process_item) or the sorted sweep
-// (process_item_sweep) on each. DLO..DHI: embedding dimensions compiled in (one specialised d, or
-// all of 1..5 with a switch); Q: queries per thread; KS: top-k slots (k + 1 rounded up).
+// (process_item_sweep) on each. DLO..DHI: embedding dimensions compiled in (one specialised d = 1..8,
+// or all of 1..5 with a switch); Q: queries per thread; KS: top-k slots (k + 1 rounded up).
 #pragma once
 
 #include "te_sweep.cuh"
@@ -65,6 +65,18 @@ __global__ void __launch_bounds__(kBatchedMaxThreads) batched_kernel(const Batch
             if (ks == 5) return sweep ? (const void*)batched_kernel<DLO, DHI, 4, 5, true>        \
                                       : (const void*)batched_kernel<DLO, DHI, 4, 5, false>;      \
         }                                                                                        \
+        return nullptr;                                                                          \
+    }
+
+// d = 6..8 (joint dimension 13..17): one query per thread (the duplicated coordinates of two
+// queries plus four references' would not fit the register budget)
+#define TE_BATCHED_PTR_FN_WIDE(NAME, DD)                                                         \
+    const void* NAME(int ks, int q, bool sweep) {                                                \
+        if (q != 1) return nullptr;                                                              \
+        if (ks == 5) return sweep ? (const void*)batched_kernel<DD, DD, 1, 5, true>              \
+                                  : (const void*)batched_kernel<DD, DD, 1, 5, false>;            \
+        if (ks == 17) return sweep ? (const void*)batched_kernel<DD, DD, 1, 17, true>            \
+                                   : (const void*)batched_kernel<DD, DD, 1, 17, false>;          \
         return nullptr;                                                                          \
     }
 

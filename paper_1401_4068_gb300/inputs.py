@@ -349,12 +349,13 @@ def ar1_analysis(name: str = "unidirectional", S: int = 500, R: int = 50, window
 #   dW_i/dt = U_i V_i - beta W_i
 # The paper analyses the V coordinates and states gamma_XY = 0.3, delta = 45 ms, 1 kHz sampling,
 # but not sigma, rho, beta, the solver's time scale or the initial states: those below are this
-# implementation's choices (classic Lorenz constants; one sample = 0.01 model time units, so the
-# coupling delay is 0.45 units = 45 samples; random initial states relaxed for 1000 samples).
+# implementation's choices (classic Lorenz constants; one sample = 0.02 model time units, so the
+# coupling delay is 0.9 units = 45 samples and the autocorrelation of V falls to 1/e within about
+# 8 samples; random initial states relaxed for 1000 samples).
 LORENZ_SIGMA = 10.0
 LORENZ_BETA = 8.0 / 3.0
 LORENZ_RHO = (28.0, 28.0)      # rho_X, rho_Y
-LORENZ_DT = 0.01               # model time units per sample
+LORENZ_DT = 0.02               # model time units per sample
 LORENZ_SUBSTEPS = 4            # fourth-order Runge-Kutta steps per sample
 LORENZ_DELAY = 45              # delta_XY in samples
 LORENZ_GAMMA = 0.3
@@ -363,7 +364,7 @@ LORENZ_BURN = 1000
 
 def lorenz_pair(rng: np.random.Generator, R: int, T: int, gamma: float = LORENZ_GAMMA,
                 delay: int = LORENZ_DELAY, coupled=(1000, 2000), burn: int = LORENZ_BURN,
-                substeps: int = LORENZ_SUBSTEPS):
+                substeps: int = LORENZ_SUBSTEPS, dt: float = None):
     """R repetitions of T samples of the Eq. 11 pair; returns (src = V_X, tgt = V_Y) float32.
 
     ``coupled``: kept-sample interval [a, b) in which gamma_XY = gamma (None: all samples,
@@ -372,7 +373,7 @@ def lorenz_pair(rng: np.random.Generator, R: int, T: int, gamma: float = LORENZ_
     midpoint is the mean of the two neighbouring grid values (linear interpolation), and before
     the first ``delay`` samples the history is the initial state (a constant initial function).
     """
-    h = LORENZ_DT / substeps
+    h = (dt or LORENZ_DT) / substeps
     lag = delay * substeps                      # delay in grid steps
     rho = np.array(LORENZ_RHO).reshape(2, 1)
     u = rng.uniform(-15.0, 15.0, (2, R))
@@ -412,21 +413,22 @@ def lorenz_pair(rng: np.random.Generator, R: int, T: int, gamma: float = LORENZ_
     return np.ascontiguousarray(out[0]), np.ascontiguousarray(out[1])
 
 
-# Embedding of the Lorenz V coordinates (the paper uses "optimal" parameters without stating
-# them; its benchmark chunk has 17 = 1 + 2 * 8 joint coordinates, so d = 8 there).
-LORENZ_D = 3
-LORENZ_TAU = 8
+# Embedding of the Lorenz V coordinates for the analyses (the paper uses "optimal" parameters
+# without stating them): d = 4 and tau = 3 samples, about half the autocorrelation time. The
+# paper's benchmark chunk has 17 = 1 + 2 * 8 joint coordinates, so d = 8 there.
+LORENZ_D = 4
+LORENZ_TAU = 3
 
 
 def lorenz_analysis(S: int = 500, R: int = 150, T: int = 3000, d: int = LORENZ_D, tau: int = LORENZ_TAU,
-                    seed: int = 0) -> Workload:
+                    seed: int = 0, dt: float = None) -> Workload:
     """The paper's non-stationary Lorenz analysis (Fig. 6): 150 repetitions x 3000 samples, coupling
     gamma_XY = 0.3 with delay 45 samples during samples 1000..2000 only, analysis windows
     200..450, 1600..1850 and 2750..3000 (250 samples), delays scanned over 35..55, S surrogates,
     k = 4.  The instances hold the original and surrogates at the true delay; a delay scan
     supplies u."""
     rng = np.random.default_rng(BASE_SEED + 80 + seed)
-    src, tgt = lorenz_pair(rng, R, T)
+    src, tgt = lorenz_pair(rng, R, T, dt=dt)
     perms = permutations(rng, S, R)
     s = Series(src, tgt, d=d, tau=tau, u=LORENZ_DELAY, perms=perms)
     ts = [t for t in (200, 1600, 2750) if t + 250 <= T]
@@ -436,14 +438,14 @@ def lorenz_analysis(S: int = 500, R: int = 150, T: int = 3000, d: int = LORENZ_D
 
 
 def lorenz_robustness(S: int = 100, R: int = 300, d: int = LORENZ_D, tau: int = LORENZ_TAU,
-                      trials=(3, 10, 25, 50, 150), seed: int = 0):
+                      trials=(3, 10, 25, 50, 150), seed: int = 0, dt: float = None):
     """The robustness analysis (Fig. 8): coupled Lorenz systems (gamma_XY = 0.3 throughout, delay
     45 samples), repetitions of 300 samples, delays scanned over 30..60.  The paper takes the
     first M = 500 .. 30000 embedded points; here a point set is the first R_M whole repetitions
     over the window 100..299 (200 points each): M = 600, 2000, 5000, 10000, 30000.
     Returns {M: Workload} (one series per M, the first R_M repetitions, S surrogates each)."""
     rng = np.random.default_rng(BASE_SEED + 90 + seed)
-    src, tgt = lorenz_pair(rng, R, 300, coupled=None)
+    src, tgt = lorenz_pair(rng, R, 300, coupled=None, dt=dt)
     out = {}
     for r_m in trials:
         perms = permutations(rng, S, r_m)
