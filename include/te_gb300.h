@@ -221,7 +221,7 @@ te_status te_last_work(te_handle* h, uint64_t* pairs, uint64_t* ops, int32_t* sw
  * estimates whose joint points share the target part y_t, y- (same target series, repetitions,
  * window start, window, d and tau; they differ only in the source part x-: the original and its
  * trial-shuffled surrogates of Fig. 3, and every scanned delay u of Eq. 5) are processed in
- * bundles of up to 4 that fit shared memory together. A bundle is staged once and the target
+ * bundles of up to 3 that fit shared memory together. A bundle is staged once and the target
  * part of every distance and count is computed once for all of its members. The paper computes
  * each surrogate separately; this is exact because max is exact: each member sees the same FP32
  * differences the unshared search computes. Applies with k <= 4 to one embedding dimension per

@@ -344,9 +344,10 @@ __device__ __forceinline__ void bundle_warp_block(const BatchArgs& a, const Inst
 }
 
 // The bundle kernel: a CTA takes a bundle (its leader's work item) from the queue, stages it,
-// and its warps take 32*Q-query blocks from a CTA-local counter.
+// and its warps take 32*Q-query blocks from a CTA-local counter. Three CTAs per SM for d <= 3
+// (a C3-sized bundle, 1200 points x 13 columns, takes 62 KB of shared memory), two above.
 template <int d, int Q, int KS, int M>
-__global__ void __launch_bounds__(kBundleThreads) bundle_kernel(const BatchArgs a) {
+__global__ void __launch_bounds__(kBundleThreads, d <= 3 ? 3 : 2) bundle_kernel(const BatchArgs a) {
     extern __shared__ __align__(16) float sm[];
     __shared__ int s_item;
     __shared__ int s_wblock;

@@ -108,7 +108,7 @@ cudaError_t launch_batched(const BatchedVariant& v, const BatchArgs& a, int grid
                            size_t smem, cudaStream_t s);
 
 // ---- the bundle kernel (te_bundle.cu): estimates sharing one target part, sorted sweep ----
-constexpr int kBundleMax = 4;       // members per bundle
+constexpr int kBundleMax = 3;       // members per bundle
 constexpr int kBundleQ = 1;         // queries per thread
 constexpr int kBundleThreads = 256;
 const void* bundle_kernel_ptr(int d, int ks);

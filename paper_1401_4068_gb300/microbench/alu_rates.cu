@@ -9,7 +9,11 @@
 // |x| per instruction), set.lt.f32.f32 (1.0f / 0.0f), fma.f32, and the coordinate pairs
 //   one coordinate:   sub.f32 + abs + max.f32
 //   two coordinates:  sub.f32x2 + max.abs.f32 (three inputs)
-// and the count step: set.lt.f32.f32 + add.f32.
+// and the count step: set.lt.f32.f32 + add.f32. Integer forms: add.u32, and.b32, min.u32,
+// shr.u32 + add.u32 (a sign bit accumulated), and the count step written as an FP32 subtraction
+// whose sign bit is accumulated: b < e exactly when fl(b - e) has its sign bit set (fl(b - e) is
+// +0 when b == e), so [b < e] = sign(fl(b - e)); "count x2" is the n_xz form (two such
+// subtractions, their sign bits ANDed, then accumulated).
 #include <cstdio>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -21,19 +25,23 @@ constexpr int kIters = 8192;
 constexpr int kChains = 8;
 constexpr int kThreads = 256;
 
-enum Op { OP_FADD, OP_FSUB2, OP_FMAX, OP_FMAX3_ABS, OP_FSET, OP_FFMA, OP_COORD1, OP_COORD2, OP_COUNT };
+enum Op { OP_FADD, OP_FSUB2, OP_FMAX, OP_FMAX3_ABS, OP_FSET, OP_FFMA, OP_COORD1, OP_COORD2, OP_COUNT,
+          OP_IADD, OP_LOP, OP_IMIN, OP_SHRADD, OP_COUNT_SIGN, OP_COUNT_SIGN2 };
 
 template <int OP>
 __global__ void __launch_bounds__(kThreads) rate_kernel(float* out, float seed) {
     float a[kChains];
+    unsigned ua[kChains];
     unsigned long long v[kChains];
 #pragma unroll
     for (int c = 0; c < kChains; ++c) {
         a[c] = seed * (float)(threadIdx.x + c);
+        ua[c] = threadIdx.x * 7u + c;
         v[c] = ((unsigned long long)__float_as_uint(a[c] + 1.5f) << 32) | __float_as_uint(a[c] + 0.5f);
     }
     const float b = seed * 0.5f, b2 = seed * 0.25f;
     const unsigned long long bb = ((unsigned long long)__float_as_uint(b2) << 32) | __float_as_uint(b);
+    const unsigned ub = __float_as_uint(seed) | 1u;
 #pragma unroll 1
     for (int it = 0; it < kIters; ++it) {
 #pragma unroll
@@ -56,11 +64,27 @@ __global__ void __launch_bounds__(kThreads) rate_kernel(float* out, float seed) 
             if (OP == OP_COUNT)
                 asm volatile("{.reg .f32 s; set.lt.f32.f32 s, %1, %2; add.rn.f32 %0, %0, s;}"
                              : "+f"(a[c]) : "f"(b2 + a[c]), "f"(b));
+            if (OP == OP_IADD) asm volatile("add.u32 %0, %0, %1;" : "+r"(ua[c]) : "r"(ub));
+            if (OP == OP_LOP) asm volatile("xor.b32 %0, %0, %1;" : "+r"(ua[c]) : "r"(ub));
+            if (OP == OP_IMIN) asm volatile("min.u32 %0, %0, %1;" : "+r"(ua[c]) : "r"(ub + (unsigned)c));
+            if (OP == OP_SHRADD)
+                asm volatile("{.reg .u32 t; shr.u32 t, %1, 31; add.u32 %0, %0, t;}"
+                             : "+r"(ua[c]) : "r"(ua[c] ^ ub));
+            // the difference depends on the chain's previous value, so nothing is hoisted
+            if (OP == OP_COUNT_SIGN)
+                asm volatile("{.reg .f32 d; .reg .u32 t; sub.rn.f32 d, %1, %2; mov.b32 t, d; shr.u32 t, t, 31;"
+                             " add.u32 %0, %0, t;}"
+                             : "+r"(ua[c]) : "f"(__uint_as_float(ua[c] & 0x3fffffffu)), "f"(b));
+            if (OP == OP_COUNT_SIGN2)
+                asm volatile("{.reg .f32 d, e; .reg .u32 t, w; sub.rn.f32 d, %1, %2; sub.rn.f32 e, %3, %2;"
+                             " mov.b32 t, d; mov.b32 w, e; and.b32 t, t, w; shr.u32 t, t, 31; add.u32 %0, %0, t;}"
+                             : "+r"(ua[c]) : "f"(__uint_as_float(ua[c] & 0x3fffffffu)), "f"(b),
+                               "f"(__uint_as_float((ua[c] >> 1) & 0x3fffffffu)));
         }
     }
     float s = 0.f;
 #pragma unroll
-    for (int c = 0; c < kChains; ++c) s += a[c] + __uint_as_float((unsigned)v[c]);
+    for (int c = 0; c < kChains; ++c) s += a[c] + __uint_as_float((unsigned)v[c]) + (float)ua[c];
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
@@ -139,6 +163,12 @@ int main() {
     rc |= run<OP_COORD1>("coordinate: sub + abs + max", sms, out, 0, 0, 1);
     rc |= run<OP_COORD2>("2 coordinates: sub.f32x2 + max.abs (3 inputs)", sms, out, 0, 0, 2);
     rc |= run<OP_COUNT>("count: set.lt.f32.f32 + add.f32", sms, out, 0, 2, 0);
+    rc |= run<OP_IADD>("add.u32", sms, out, 0, 1, 0);
+    rc |= run<OP_LOP>("xor.b32", sms, out, 0, 1, 0);
+    rc |= run<OP_IMIN>("min.u32", sms, out, 0, 1, 0);
+    rc |= run<OP_SHRADD>("shr.u32 31 + add.u32 (per pair)", sms, out, 0, 1, 0);
+    rc |= run<OP_COUNT_SIGN>("count: sub.f32 + sign-bit accumulate (per count)", sms, out, 0, 1, 0);
+    rc |= run<OP_COUNT_SIGN2>("count x2: 2 sub.f32 + and + sign accumulate (per count)", sms, out, 0, 1, 0);
     printf("}}\n");
     return rc;
 }

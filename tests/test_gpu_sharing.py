@@ -1,8 +1,9 @@
 """Target-part sharing (the bundle kernel): estimates that share y_t and y- (the original and its
 trial-shuffled surrogates, every scanned delay u) run in bundles that compute the target part of
 each distance and count once. Per-point radii and counts must equal the unshared search and the
-CPU oracle bit for bit, TE within 1e-6 nats of the oracle; bundles of every size 2..4, ragged
-point counts, mixed embedding dimensions, the delay scan and a bad permutation entry."""
+CPU oracle bit for bit, TE within 1e-6 nats of the oracle; bundles of every size 2..3, ragged
+point counts, mixed embedding dimensions, the delay scan and a bad permutation entry.
+Bundles hold up to 3 estimates (never 1: a remainder of one turns the last two bundles into 2 + 2)."""
 import numpy as np
 import pytest
 import torch
@@ -37,11 +38,11 @@ def _oracle_check(series, insts, k, res):
 
 
 def test_shared_equals_unshared_and_oracle(te_handle):
-    w = I.config(3, n_t=2, S=9)  # 10 estimates per start: bundles of 4, 4, 2
+    w = I.config(3, n_t=2, S=9)  # 10 estimates per start: bundles of 3, 3, 2, 2
     ds = te.to_device(w.series)
     off, b0, ops0, alg0, _ = _estimate(te_handle, ds, w.instances, w.k, False)
     on, b1, ops1, alg1, swept = _estimate(te_handle, ds, w.instances, w.k, True)
-    assert swept and b0 == 0 and b1 == 6
+    assert swept and b0 == 0 and b1 == 8
     assert ops0 == alg0 and ops1 < alg1
     assert torch.equal(off["counts"], on["counts"]) and torch.equal(off["eps"], on["eps"])
     assert torch.max(torch.abs(off["te"] - on["te"])).item() <= 1e-12
@@ -49,7 +50,7 @@ def test_shared_equals_unshared_and_oracle(te_handle):
     sub = [w.instances[i] for i in idx]
     res = te.te_estimate(te_handle, ds, sub, w.k, want_err=True, want_counts=True)
     torch.cuda.synchronize()
-    assert te.te_last_alu_ops(te_handle)[1] == 2  # starts 0 and 1: {0,1,4,9}, {10,15,19}
+    assert te.te_last_alu_ops(te_handle)[1] == 3  # starts 0 and 1: {0,1}, {4,9}, {10,15,19}
     _oracle_check(w.series, sub, w.k, res)
 
 
@@ -58,7 +59,7 @@ def test_every_bundle_size_and_ragged_point_counts(te_handle, R, window):
     rng = np.random.default_rng(100 + R)
     src, tgt = I.ar2_pair(rng, R, 120)
     s = I.Series(src, tgt, d=3, tau=1, u=5, perms=I.permutations(rng, 9, R))
-    # starts with 2, 3, 5, 6 and 9 estimates: bundles 2 | 3 | 3+2 | 4+2 | 4+3+2
+    # starts with 2, 3, 5, 6 and 9 estimates: bundles 2 | 3 | 3+2 | 3+3 | 3+3+3
     sizes = {20: 2, 30: 3, 40: 5, 50: 6, 60: 9}
     insts = [I.Instance(0, t, window, p) for t, n in sizes.items() for p in range(-1, n - 1)]
     ds = te.to_device([s])
