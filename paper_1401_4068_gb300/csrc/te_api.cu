@@ -120,6 +120,7 @@ struct Plan {
     std::vector<int32_t> members;
     int bd = 0, bgrid = 0, n_bundled = 0;
     size_t bsmem = 0;
+    uint64_t table_hash = 0;  // of the device tables (instances, items, bundles): part of the graph key
 };
 
 struct DeviceGuard {
@@ -134,9 +135,17 @@ struct DeviceGuard {
     }
 };
 
+// 64-bit hash of a byte range, eight bytes per step (FNV-style multiply with an extra shift mix)
 uint64_t fnv(uint64_t h, const void* data, size_t n) {
     const unsigned char* c = static_cast<const unsigned char*>(data);
-    for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    size_t i = 0;
+    for (; i + 8 <= n; i += 8) {
+        uint64_t w;
+        std::memcpy(&w, c + i, 8);
+        h = (h ^ w) * 1099511628211ull;
+        h ^= h >> 29;
+    }
+    for (; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
     return h;
 }
 
@@ -153,6 +162,7 @@ struct te_handle {
     int last_launches = 0;
     int cfg_threads = 0, cfg_qpt = 0;
     std::map<std::string, std::pair<int, int>> tuned;  // batch signature -> (threads, qpt)
+    int tune_gen = 0;                                   // bumped whenever `tuned` changes
     bool per_instance = false;  // one launch per instance instead of one persistent launch
     int search_mode = 1;        // 1: sorted sweep where it applies, 0: exhaustive search
     bool sharing = true;        // bundles of estimates with one target part (sweep mode)
@@ -173,6 +183,13 @@ struct te_handle {
     DevBuf<int32_t> d_members;
     HostBuf<unsigned char> h_stage;
     int workspace_gen = 0;
+
+    // the last plan and the exact inputs it was built from: an identical call reuses it
+    std::vector<te_series> pc_series;
+    std::vector<te_instance> pc_inst;
+    std::vector<int> pc_cfg;
+    bool pc_valid = false;
+    Plan plan;
 
     uint64_t graph_key = 0;
     int graph_gen = -1;
@@ -529,7 +546,37 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
         if (bper < 1) return h->fail(TE_ENOTIMPL, "bundle kernel does not fit: smem=%zu", P->bsmem);
         P->bgrid = (int)std::min<int64_t>((int64_t)bper * h->sm_count, (int64_t)P->bitems.size());
     }
+    uint64_t th = 1469598103934665603ull;
+    th = fnv(th, P->insts.data(), P->insts.size() * sizeof(InstDesc));
+    th = fnv(th, P->items.data(), P->items.size() * sizeof(WorkItem));
+    th = fnv(th, P->bitems.data(), P->bitems.size() * sizeof(WorkItem));
+    th = fnv(th, P->members.data(), P->members.size() * sizeof(int32_t));
+    P->table_hash = th;
     (void)nmax;
+    return TE_OK;
+}
+
+// The handle's plan for this batch: reused when the series array, the instances, k and every
+// setting that shapes a plan equal those of the previous call byte for byte, else rebuilt.
+te_status cached_plan(te_handle* h, const te_series* series, int n_series, const te_instance* inst, int n_inst,
+                      int k, Plan** out) {
+    std::vector<int> cfg = {k, h->search_mode, h->sharing ? 1 : 0, h->per_instance ? 1 : 0, h->cfg_threads,
+                            h->cfg_qpt, h->tune_gen, h->sm_count};
+    const bool hit = h->pc_valid && h->pc_cfg == cfg && (int)h->pc_series.size() == n_series &&
+                     (int)h->pc_inst.size() == n_inst &&
+                     std::memcmp(h->pc_series.data(), series, sizeof(te_series) * (size_t)n_series) == 0 &&
+                     std::memcmp(h->pc_inst.data(), inst, sizeof(te_instance) * (size_t)n_inst) == 0;
+    if (!hit) {
+        h->pc_valid = false;
+        h->plan = Plan();
+        te_status st = build_plan(h, series, n_series, inst, n_inst, k, &h->plan);
+        if (st != TE_OK) return st;
+        h->pc_series.assign(series, series + n_series);
+        h->pc_inst.assign(inst, inst + n_inst);
+        h->pc_cfg = cfg;
+        h->pc_valid = true;
+    }
+    *out = &h->plan;
     return TE_OK;
 }
 
@@ -687,11 +734,7 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
     double* te_dst = n_groups > 0 ? h->d_te_all.p : te_out;
 
     // signature of everything the captured graph bakes in
-    uint64_t key = 1469598103934665603ull;
-    key = fnv(key, P.insts.data(), P.insts.size() * sizeof(InstDesc));
-    key = fnv(key, P.items.data(), P.items.size() * sizeof(WorkItem));
-    key = fnv(key, P.bitems.data(), P.bitems.size() * sizeof(WorkItem));
-    key = fnv(key, P.members.data(), P.members.size() * sizeof(int32_t));
+    uint64_t key = P.table_hash;
     const void* outs[] = {te_out, err, counts, eps, te_orig, te_surr, p};
     key = fnv(key, outs, sizeof outs);
     const int cfg[] = {k, P.threads, P.grid, P.smem_floats, P.var.dlo, P.var.dhi, P.var.ks, P.var.qpt,
@@ -947,9 +990,9 @@ TE_EXPORT te_status te_estimate(te_handle* h, const te_series* series, int32_t n
         return TE_OK;
     }
     DeviceGuard g(h->device);
-    Plan P;
-    if ((st = build_plan(h, series, n_series, inst, n_inst, k, &P)) != TE_OK) return st;
-    return run_batched(h, P, series, n_series, inst, n_inst, k, te, err_bound, counts, eps, 0, 0, nullptr,
+    Plan* P = nullptr;
+    if ((st = cached_plan(h, series, n_series, inst, n_inst, k, &P)) != TE_OK) return st;
+    return run_batched(h, *P, series, n_series, inst, n_inst, k, te, err_bound, counts, eps, 0, 0, nullptr,
                        nullptr, nullptr, static_cast<cudaStream_t>(stream));
 }
 
@@ -978,9 +1021,9 @@ TE_EXPORT te_status te_surrogate_test(te_handle* h, const te_series* series, int
         for (int j = 0; j < n_t; ++j)
             for (int m = -1; m < S; ++m) inst.push_back(te_instance{s, t_starts[j], window, m});
     DeviceGuard g(h->device);
-    Plan P;
-    if ((st = build_plan(h, series, n_series, inst.data(), (int)inst.size(), k, &P)) != TE_OK) return st;
-    return run_batched(h, P, series, n_series, inst.data(), (int)inst.size(), k, nullptr, nullptr, nullptr,
+    Plan* P = nullptr;
+    if ((st = cached_plan(h, series, n_series, inst.data(), (int)inst.size(), k, &P)) != TE_OK) return st;
+    return run_batched(h, *P, series, n_series, inst.data(), (int)inst.size(), k, nullptr, nullptr, nullptr,
                        nullptr, n_series * n_t, S, te_orig, te_surr, p, static_cast<cudaStream_t>(stream));
 }
 
@@ -993,8 +1036,8 @@ bool load_tune_cache(te_handle* h, const char* path) {
     int t = 0, q = 0;
     while (fgets(line, sizeof line, f)) {
         if (sscanf(line, " \"%127[^\"]\": {\"threads\": %d, \"qpt\": %d", key, &t, &q) == 3 && t >= 64 &&
-            t <= te::kBatchedMaxThreads && t % 32 == 0 && (q == 2 || q == 4))
-            h->tuned[key] = {t, q};
+            t <= te::kBatchedMaxThreads && t % 32 == 0 && (q == 1 || q == 2 || q == 4))
+            h->tuned[key] = {t, q}, ++h->tune_gen;
     }
     fclose(f);
     return true;
@@ -1122,6 +1165,7 @@ TE_EXPORT te_status te_autotune(te_handle* h, const te_series* series, int32_t n
         h->err.clear();
         if (!bt) return h->fail(TE_ECUDA, "te_autotune: no candidate ran");
         h->tuned[sig] = {bt, bq};
+        ++h->tune_gen;
         best_ms[sig] = best;
         if (cache_path && cache_path[0] && !save_tune_cache(h, cache_path, best_ms))
             return h->fail(TE_EINVAL, "te_autotune: cannot write %s", cache_path);
@@ -1157,8 +1201,8 @@ TE_EXPORT te_status te_delay_scan(te_handle* h, const te_series* series, const i
         for (int j = 0; j < n_t; ++j)
             for (int m = -1; m < S; ++m) inst.push_back(te_instance{iu, t_starts[j], window, m});
     DeviceGuard g(h->device);
-    Plan P;
-    if ((st = build_plan(h, ser.data(), n_u, inst.data(), (int)inst.size(), k, &P)) != TE_OK) return st;
+    Plan* P = nullptr;
+    if ((st = cached_plan(h, ser.data(), n_u, inst.data(), (int)inst.size(), k, &P)) != TE_OK) return st;
     const int n_groups = n_u * n_t;
     bool grew = false;
     cudaError_t e;
@@ -1167,7 +1211,7 @@ TE_EXPORT te_status te_delay_scan(te_handle* h, const te_series* series, const i
         return h->fail(TE_ENOMEM, "te_delay_scan workspace: %s", cudaGetErrorString(e));
     if (grew) ++h->workspace_gen;
     cudaStream_t strm = static_cast<cudaStream_t>(stream);
-    st = run_batched(h, P, ser.data(), n_u, inst.data(), (int)inst.size(), k, nullptr, nullptr, nullptr, nullptr,
+    st = run_batched(h, *P, ser.data(), n_u, inst.data(), (int)inst.size(), k, nullptr, nullptr, nullptr, nullptr,
                      n_groups, S, te, S > 0 ? h->d_surr_ws.p : nullptr, p ? p : h->d_p_ws.p, strm);
     if (st != TE_OK) return st;
     if ((e = te::launch_delay_argmax(te, n_u, n_t, u_lo, u_best, strm)) != cudaSuccess)

@@ -299,3 +299,31 @@ def test_sorted_sweep_equals_exhaustive_search(te_handle, case):
     assert torch.equal(ref["counts"], got["counts"]) and torch.equal(ref["eps"], got["eps"])
     assert torch.max(torch.abs(ref["te"] - got["te"])).item() <= 1e-9
     assert 0 < sw_pairs <= ex_pairs
+
+
+def test_plan_reuse_follows_the_inputs(te_handle):
+    """A call identical to the previous one reuses its plan; a changed instance, series field or
+    setting must give a new plan (results of the new inputs, checked against the oracle)."""
+    w = I.config(3, n_t=2, S=6, R=120)
+    ds = te.to_device(w.series)
+    a = te.te_estimate(te_handle, ds, w.instances, w.k).clone()
+    b = te.te_estimate(te_handle, ds, w.instances, w.k).clone()
+    insts = list(w.instances)
+    insts[3] = I.Instance(0, insts[3].t_start, insts[3].window, 5 if insts[3].perm != 5 else 4)
+    c = te.te_estimate(te_handle, ds, insts, w.k).clone()
+    s2 = w.series[0]
+    ds2 = [te.DeviceSeries(ds[0].src, ds[0].tgt, ds[0].d, ds[0].tau, ds[0].u + 1, ds[0].perms)]  # same buffers
+    d = te.te_estimate(te_handle, ds2, w.instances, w.k).clone()
+    te.te_set_search(te_handle, False)
+    try:
+        e = te.te_estimate(te_handle, ds, w.instances, w.k).clone()
+    finally:
+        te.te_set_search(te_handle, True)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    o_c = oracle.te_batch(w.series, insts, w.k)
+    assert np.max(np.abs(c.cpu().numpy() - o_c)) <= TOL
+    su = I.Series(s2.src, s2.tgt, d=s2.d, tau=s2.tau, u=s2.u + 1, perms=s2.perms)
+    o_d = oracle.te_batch([su], w.instances, w.k)
+    assert np.max(np.abs(d.cpu().numpy() - o_d)) <= TOL
+    assert torch.max(torch.abs(a - e)).item() <= 1e-9
