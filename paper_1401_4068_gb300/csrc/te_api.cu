@@ -521,6 +521,19 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
             I.sort_off = f->second;
         }
     }
+    // every unshared estimate staged whole with one d <= 2: the warp-mode sweep kernel (1024-thread
+    // CTAs unless a shape was set or tuned for this signature)
+    bool all_warp = !P->items.empty();
+    for (int i = 0; i < n_inst; ++i)
+        if (!bundled[i] && !P->insts[i].warp_mode) all_warp = false;
+    if (sweep && !h->per_instance && all_warp && dlo == dhi && dlo <= 2 && ks == 5) {
+        P->var.warp_only = true;
+        if (!h->cfg_threads && h->tuned.find(shape_signature(P->insts, ks)) == h->tuned.end())
+            threads = te::kSweepWarpThreads;
+    } else if (threads > te::kBatchedMaxThreads) {
+        threads = te::kBatchedMaxThreads;
+    }
+    P->threads = threads;
     // bound on the summation error relative to sum |terms| (see te_estimate in the header):
     // 3*qpt float-float additions per thread (<= 2^-46 each), table rounding (2^-47), FP64
     // reductions over threads and items
@@ -738,6 +751,7 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
     const void* outs[] = {te_out, err, counts, eps, te_orig, te_surr, p};
     key = fnv(key, outs, sizeof outs);
     const int cfg[] = {k, P.threads, P.grid, P.smem_floats, P.var.dlo, P.var.dhi, P.var.ks, P.var.qpt,
+                       P.var.warp_only ? 1 : 0,
                        n_groups, S, h->profiling ? 1 : 0, n_inst, P.var.sweep ? 1 : 0, P.bd, P.bgrid,
                        (int)P.bsmem};
     key = fnv(key, cfg, sizeof cfg);
@@ -1036,7 +1050,7 @@ bool load_tune_cache(te_handle* h, const char* path) {
     int t = 0, q = 0;
     while (fgets(line, sizeof line, f)) {
         if (sscanf(line, " \"%127[^\"]\": {\"threads\": %d, \"qpt\": %d", key, &t, &q) == 3 && t >= 64 &&
-            t <= te::kBatchedMaxThreads && t % 32 == 0 && (q == 1 || q == 2 || q == 4))
+            t <= te::kSweepWarpThreads && t % 32 == 0 && (q == 1 || q == 2 || q == 4))
             h->tuned[key] = {t, q}, ++h->tune_gen;
     }
     fclose(f);
@@ -1122,12 +1136,13 @@ TE_EXPORT te_status te_autotune(te_handle* h, const te_series* series, int32_t n
         h->profiling = true;
         for (int q : qs) {
             int64_t min_slots = INT64_MAX;
+            const int tmax = P.var.warp_only ? te::kSweepWarpThreads : te::kBatchedMaxThreads;
             if (uniform)
-                for (int t = 64; t <= te::kBatchedMaxThreads; t += 32) {
+                for (int t = 64; t <= tmax; t += 32) {
                     const int64_t per = (int64_t)t * q;
                     min_slots = std::min(min_slots, ((P.insts[0].N + per - 1) / per) * per);
                 }
-            for (int t = 64; t <= te::kBatchedMaxThreads; t += 32) {
+            for (int t = 64; t <= tmax; t += 32) {
                 if (uniform) {
                     const int64_t per = (int64_t)t * q;
                     if (((P.insts[0].N + per - 1) / per) * per > min_slots + min_slots / 8) continue;

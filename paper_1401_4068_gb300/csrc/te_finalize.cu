@@ -77,6 +77,12 @@ cudaError_t launch_delay_argmax(const double* te, int n_u, int n_t, int u_lo, in
 }
 
 const void* batched_kernel_ptr(const BatchedVariant& v) {
+    if (v.warp_only) {
+        if (!v.sweep || v.dlo != v.dhi) return nullptr;
+        if (v.dlo == 1) return sweep_warp_ptr_d1(v.ks, v.qpt);
+        if (v.dlo == 2) return sweep_warp_ptr_d2(v.ks, v.qpt);
+        return nullptr;
+    }
     if (v.dlo == v.dhi) {
         switch (v.dlo) {
             case 1: return batched_ptr_d1(v.ks, v.qpt, v.sweep);

@@ -49,6 +49,8 @@ struct WorkItem {
 
 // Largest CTA of the persistent batched kernel (its __launch_bounds__).
 constexpr int kBatchedMaxThreads = 512;
+// CTA of the warp-mode sweep kernel (d <= 2, every estimate resident in shared memory).
+constexpr int kSweepWarpThreads = 1024;
 
 // Bits of the device flag word.
 enum : int32_t { kFlagBadPerm = 1 };
@@ -88,7 +90,8 @@ cudaError_t launch_count(const float* pts, int N, int dy, int dx, int ld, const 
 // dhi <= 5), ks = k-slots, qpt = queries per thread (1 for d >= 6).
 struct BatchedVariant {
     int dlo, dhi, ks, qpt;
-    bool sweep;  // sorted-sweep search instead of the exhaustive one
+    bool sweep;      // sorted-sweep search instead of the exhaustive one
+    bool warp_only;  // sweep_warp_kernel: every estimate staged whole, d = dlo = dhi <= 2, ks = 5
 };
 cudaError_t launch_sort_groups(const SortGroup* groups, int n_groups, int nmax, int32_t* idx, float* key,
                                int32_t* tmp_idx, float* tmp_key, cudaStream_t s);
@@ -104,6 +107,8 @@ const void* batched_ptr_d6(int ks, int q, bool sweep);
 const void* batched_ptr_d7(int ks, int q, bool sweep);
 const void* batched_ptr_d8(int ks, int q, bool sweep);
 const void* batched_ptr_mix(int ks, int q, bool sweep);
+const void* sweep_warp_ptr_d1(int ks, int q);
+const void* sweep_warp_ptr_d2(int ks, int q);
 cudaError_t launch_batched(const BatchedVariant& v, const BatchArgs& a, int grid, int threads,
                            size_t smem, cudaStream_t s);
 

@@ -52,6 +52,34 @@ __global__ void __launch_bounds__(kBatchedMaxThreads) batched_kernel(const Batch
     }
 }
 
+// Sweep kernel for batches whose every estimate is staged whole in shared memory (warp mode)
+// with d <= 2: without the tiled path it fits 64 registers, so a CTA can have 1024 threads, twice
+// the warps per SM when one large instance (an AR(1) window of 15,000 points) fills shared memory.
+template <int DD, int Q, int KS>
+__global__ void __launch_bounds__(kSweepWarpThreads) sweep_warp_kernel(const BatchArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    __shared__ int s_item;
+    __shared__ int s_wblock;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int ticket = s_item;
+        if (ticket >= a.n_items) break;
+        const WorkItem w = a.items[a.item_base + ticket];
+        const InstDesc I = a.insts[w.inst];
+        process_instance_sweep_warps<DD, Q, KS>(a, I, w.q0, sm, &s_wblock);
+    }
+}
+
+#define TE_SWEEP_WARP_PTR_FN(NAME, DD)                                                           \
+    const void* NAME(int ks, int q) {                                                            \
+        if (ks != 5) return nullptr;                                                             \
+        if (q == 2) return (const void*)sweep_warp_kernel<DD, 2, 5>;                             \
+        if (q == 1) return (const void*)sweep_warp_kernel<DD, 1, 5>;                             \
+        return nullptr;                                                                          \
+    }
+
 // kernel pointer of one variant (defined in te_batched_*.cu); k > 4 runs with 2 queries per
 // thread only (17 slots x 4 queries would not fit the register budget)
 #define TE_BATCHED_PTR_FN(NAME, DLO, DHI)                                                        \
