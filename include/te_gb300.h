@@ -169,8 +169,10 @@ te_status te_last_kernel_ms(te_handle* h, float* ms);
 int32_t te_last_launch_count(const te_handle* h);
 
 /* Launch-configuration control for the batched kernel (used by the autotuner and tests).
- * threads: CTA size (multiple of 32, 64..512) or 0 for the built-in choice; qpt: queries per
- * thread (2 or 4) or 0 for automatic. Takes effect on the next te_estimate call. */
+ * threads: CTA size (multiple of 32, 64..1024; above 512 only the warp-mode sweep kernel of d <= 2
+ * uses it, other batches run with 512) or 0 for the built-in choice; qpt: queries per thread
+ * (1, 2 or 4; d >= 6 always runs 1, d <= 5 runs 2 when 1 is asked) or 0 for automatic. Takes
+ * effect on the next te_estimate / te_surrogate_test / te_delay_scan call. */
 te_status te_set_launch_config(te_handle* h, int32_t threads, int32_t qpt);
 
 /* te_delay_scan - delay reconstruction (Eq. 5, "Reconstruction of information transfer delays"):

@@ -294,6 +294,7 @@ void choose_shape(te_handle* h, const std::vector<InstDesc>& insts, int ks, int*
     // query per thread
     int q = (ks == 5 && dmax <= 4 && h->search_mode == 0) ? 4 : 2;
     if (h->cfg_qpt) q = ks == 5 ? h->cfg_qpt : 2;
+    if (q == 1) q = 2;  // d <= 5 has no one-query variant
     if (dmax > 5) q = 1;
     *qpt = q;
     if (h->cfg_threads) {
@@ -375,6 +376,10 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
     const int ks = k <= 4 ? 5 : 17;
     int threads, qpt;
     choose_shape(h, P->insts, ks, &threads, &qpt);
+    // CTAs above kBatchedMaxThreads exist only for the warp-mode sweep kernel, decided once the
+    // items are known: the items of tiled estimates are cut for the clamped size
+    const int asked_threads = threads;
+    threads = std::min(threads, te::kBatchedMaxThreads);
     P->var = BatchedVariant{dlo == dhi ? dlo : 1, dlo == dhi ? dhi : 5, ks, qpt};
     P->threads = threads;
     // work items: instances in descending cost (N^2 D), items of one instance contiguous
@@ -528,10 +533,8 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
         if (!bundled[i] && !P->insts[i].warp_mode) all_warp = false;
     if (sweep && !h->per_instance && all_warp && dlo == dhi && dlo <= 2 && ks == 5) {
         P->var.warp_only = true;
-        if (!h->cfg_threads && h->tuned.find(shape_signature(P->insts, ks)) == h->tuned.end())
-            threads = te::kSweepWarpThreads;
-    } else if (threads > te::kBatchedMaxThreads) {
-        threads = te::kBatchedMaxThreads;
+        const bool shaped = h->cfg_threads || h->tuned.find(shape_signature(P->insts, ks)) != h->tuned.end();
+        threads = shaped ? asked_threads : te::kSweepWarpThreads;
     }
     P->threads = threads;
     // bound on the summation error relative to sum |terms| (see te_estimate in the header):
@@ -1309,9 +1312,9 @@ TE_EXPORT te_status te_set_batching(te_handle* h, int32_t per_instance) {
 TE_EXPORT te_status te_set_launch_config(te_handle* h, int32_t threads, int32_t qpt) {
     if (!h) return TE_EINVAL;
     h->err.clear();
-    if (threads != 0 && (threads < 64 || threads > te::kBatchedMaxThreads || threads % 32))
-        return h->fail(TE_EINVAL, "threads=%d: multiple of 32 in 64..%d or 0", threads, te::kBatchedMaxThreads);
-    if (qpt != 0 && qpt != 2 && qpt != 4) return h->fail(TE_EINVAL, "qpt=%d: 2, 4 or 0", qpt);
+    if (threads != 0 && (threads < 64 || threads > te::kSweepWarpThreads || threads % 32))
+        return h->fail(TE_EINVAL, "threads=%d: multiple of 32 in 64..%d or 0", threads, te::kSweepWarpThreads);
+    if (qpt != 0 && qpt != 1 && qpt != 2 && qpt != 4) return h->fail(TE_EINVAL, "qpt=%d: 1, 2, 4 or 0", qpt);
     h->cfg_threads = threads;
     h->cfg_qpt = qpt;
     return TE_OK;

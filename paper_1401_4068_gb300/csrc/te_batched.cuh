@@ -5,8 +5,9 @@
 // One CTA takes a work item from a device queue (atomic ticket, no waits), then:
 //   1. gathers its queries' joint coordinates straight from the series (Eq. 6 / 7 with the
 //      source at t-u and the surrogate's repetition pairing) into registers;
-//   2. pass 1: streams the instance's points through shared memory in structure-of-arrays
-//      tiles and keeps, per query, the k+1 smallest max-norm distances (self included), so
+//   2. pass 1: streams the instance's points through shared memory in tiles (groups of four
+//      points, see te_device.cuh) and keeps, per query, the k+1 smallest max-norm distances
+//      (self included), so
 //      eps = the k-th neighbour distance among the other points;
 //   3. pass 2: streams the same tiles again (they stay resident when the whole instance fits)
 //      and counts points strictly inside eps in the three marginal spaces;
@@ -20,8 +21,7 @@
 namespace te {
 
 template <int d>
-__device__ __forceinline__ void stage_tile(const InstDesc& I, int base, int nv, int ldt, float* sm,
-                                           int32_t* flags) {
+__device__ __forceinline__ void stage_tile(const InstDesc& I, int base, int nv, float* sm, int32_t* flags) {
     constexpr int D = 1 + 2 * d;
     const int nfill = (nv + 3) & ~3;
     for (int p = threadIdx.x; p < nfill; p += blockDim.x) {
@@ -33,7 +33,7 @@ __device__ __forceinline__ void stage_tile(const InstDesc& I, int base, int nv, 
             for (int c = 0; c < D; ++c) v[c] = f_inf();
         }
 #pragma unroll
-        for (int c = 0; c < D; ++c) sm[c * ldt + p] = v[c];
+        for (int c = 0; c < D; ++c) sm[tile_index<D>(c, p)] = v[c];
     }
 }
 
@@ -74,9 +74,9 @@ __device__ __forceinline__ void process_item(const BatchArgs& a, const InstDesc&
         const int base = tile * ldt;
         const int nv = min(ldt, N - base);
         __syncthreads();
-        stage_tile<d>(I, base, nv, ldt, sm, a.flags);
+        stage_tile<d>(I, base, nv, sm, a.flags);
         __syncthreads();
-        if (warp_active) knn_tile<D, Q, KS>(sm, ldt, (nv + 3) >> 2, qq, t);
+        if (warp_active) knn_tile<D, Q, KS>(sm, (nv + 3) >> 2, qq, t);
     }
     float e[Q];
 #pragma unroll
@@ -91,10 +91,10 @@ __device__ __forceinline__ void process_item(const BatchArgs& a, const InstDesc&
         const int nv = min(ldt, N - base);
         if (ntile > 1) {  // a single tile is still resident from pass 1
             __syncthreads();
-            stage_tile<d>(I, base, nv, ldt, sm, a.flags);
+            stage_tile<d>(I, base, nv, sm, a.flags);
             __syncthreads();
         }
-        if (warp_active) count_tile<d, d, Q>(sm, ldt, (nv + 3) >> 2, qq, e, cz, cyz, cxz);
+        if (warp_active) count_tile<d, d, Q>(sm, (nv + 3) >> 2, qq, e, cz, cyz, cxz);
     }
 
     // ---- digamma terms of Eq. 9, compensated FP32 per thread

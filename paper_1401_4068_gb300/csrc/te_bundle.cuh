@@ -26,27 +26,29 @@ __device__ __forceinline__ float absmax_join(float a, const float (&c)[n]) {
     return absmax_range<0, n>(v);
 }
 
-// Stage a bundle in sorted order: columns 0..d hold the target part (y_t, y_{t'-1}, ...), columns
-// 1+d+m*d .. 1+d+m*d+d-1 member m's source part; +inf past the last point (a padded reference is
-// never inside any radius).
+// Stage a bundle in sorted order, in the grouped tile layout of te_device.cuh: first a tile of
+// the target part (1 + d coordinates: y_t, y_{t'-1}, ...), then one tile per member of its source
+// part (d coordinates), member m's at the float offset ng * 4 * (1 + d + m * d) (ng = groups of
+// four points); +inf past the last point (a padded reference is never inside any radius).
 template <int d, int M>
 __device__ __forceinline__ void stage_bundle(const BatchArgs& a, const InstDesc& L, const int32_t* mem, int nb,
-                                             const int32_t* __restrict__ sidx, int ldt, float* sm) {
+                                             const int32_t* __restrict__ sidx, float* sm) {
     constexpr int DA = 1 + d;
     const int N = L.N;
     const int nfill = (N + 3) & ~3;
+    const int ng = nfill >> 2;
     for (int p = threadIdx.x; p < nfill; p += blockDim.x) {
         if (p < N) {
             const int i = __ldg(sidx + p);
             const int r = i / L.W;
             const int t = L.t_start + (i - r * L.W);
             const float* y = L.tgt + (size_t)r * L.T;
-            sm[p] = __ldg(y + t);
+            sm[tile_index<DA>(0, p)] = __ldg(y + t);
 #pragma unroll
-            for (int c = 0; c < d; ++c) sm[(1 + c) * ldt + p] = __ldg(y + t - 1 - c * L.tau);
+            for (int c = 0; c < d; ++c) sm[tile_index<DA>(1 + c, p)] = __ldg(y + t - 1 - c * L.tau);
         } else {
 #pragma unroll
-            for (int c = 0; c < DA; ++c) sm[c * ldt + p] = f_inf();
+            for (int c = 0; c < DA; ++c) sm[tile_index<DA>(c, p)] = f_inf();
         }
     }
 #pragma unroll 1
@@ -55,7 +57,7 @@ __device__ __forceinline__ void stage_bundle(const BatchArgs& a, const InstDesc&
         const int32_t* perm = J.perm;
         const float* src = J.src;
         const int u = J.u, R = J.R;
-        float* col = sm + (DA + m * d) * ldt;
+        float* col = sm + ng * 4 * (DA + m * d);
         for (int p = threadIdx.x; p < nfill; p += blockDim.x) {
             if (p < N) {
                 const int i = __ldg(sidx + p);
@@ -71,10 +73,10 @@ __device__ __forceinline__ void stage_bundle(const BatchArgs& a, const InstDesc&
                 }
                 const float* x = src + (size_t)rs * L.T;
 #pragma unroll
-                for (int c = 0; c < d; ++c) col[c * ldt + p] = __ldg(x + t - u - c * L.tau);
+                for (int c = 0; c < d; ++c) col[tile_index<d>(c, p)] = __ldg(x + t - u - c * L.tau);
             } else {
 #pragma unroll
-                for (int c = 0; c < d; ++c) col[c * ldt + p] = f_inf();
+                for (int c = 0; c < d; ++c) col[tile_index<d>(c, p)] = f_inf();
             }
         }
     }
@@ -95,12 +97,12 @@ __device__ __forceinline__ void bundle_radii(const float (&t)[M][Q][KS], float (
 // pass 1 for one group of four references: the target part once, then every member's joint
 // distances, all of them before the first (branching) top-k insertion
 template <int d, int Q, int KS, int M>
-__device__ __forceinline__ void bknn_group(const float* __restrict__ s, const int (&coff)[M], int ldt, int j,
+__device__ __forceinline__ void bknn_group(const float* __restrict__ s, const int (&coff)[M], int j,
                                            const u64 (&qa)[Q][1 + d], const u64 (&qc)[M][Q][d],
                                            float (&t)[M][Q][KS]) {
     constexpr int DA = 1 + d;
     ulonglong2 ra[DA];
-    load_refs4<DA>(s, ldt, j, ra);
+    load_refs4<DA>(s, j, ra);
     float ma[Q][4];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -115,7 +117,7 @@ __device__ __forceinline__ void bknn_group(const float* __restrict__ s, const in
 #pragma unroll
     for (int m = 0; m < M; ++m) {
         ulonglong2 rc[d];
-        load_refs4<d>(s + coff[m], ldt, j, rc);
+        load_refs4<d>(s + coff[m], j, rc);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             float cx[d], cy[d], cz[d], cw[d];
@@ -136,7 +138,7 @@ __device__ __forceinline__ void bknn_group(const float* __restrict__ s, const in
 
 // pass 1 over groups [g0, g1) in direction dir (as knn_range in te_sweep.cuh)
 template <int d, int Q, int KS, int M>
-__device__ __forceinline__ int bknn_range(const float* __restrict__ s, const int (&coff)[M], int ldt, int g0, int g1,
+__device__ __forceinline__ int bknn_range(const float* __restrict__ s, const int (&coff)[M], int g0, int g1,
                                           int dir, const u64 (&qa)[Q][1 + d], const u64 (&qc)[M][Q][d],
                                           const float (&qkey)[Q], const bool (&qv)[Q], float (&t)[M][Q][KS]) {
     float r[Q], lb, rb;
@@ -146,9 +148,9 @@ __device__ __forceinline__ int bknn_range(const float* __restrict__ s, const int
 #pragma unroll 1
     for (int jj = g0; jj < g1; ++jj) {
         const int j = dir < 0 ? g1 - 1 - (jj - g0) : jj;
-        if (dir > 0 && s[ldt + 4 * j] >= rb) break;
-        if (dir < 0 && s[ldt + 4 * j + 3] <= lb) break;
-        bknn_group<d, Q, KS, M>(s, coff, ldt, j, qa, qc, t);
+        if (dir > 0 && group_key_lo<1 + d>(s, j) >= rb) break;
+        if (dir < 0 && group_key_hi<1 + d>(s, j) <= lb) break;
+        bknn_group<d, Q, KS, M>(s, coff, j, qa, qc, t);
         if ((++n & 3) == 0 && dir != 0) {
             bundle_radii<Q, KS, M>(t, r);
             warp_window(qkey, qv, r, lb, rb);
@@ -159,7 +161,7 @@ __device__ __forceinline__ int bknn_range(const float* __restrict__ s, const int
 
 // pass 2 over groups [g0, g1) ascending inside the key window [lb, rb]
 template <int d, int Q, int M>
-__device__ __forceinline__ int bcount_range(const float* __restrict__ s, const int (&coff)[M], int ldt, int g0, int g1,
+__device__ __forceinline__ int bcount_range(const float* __restrict__ s, const int (&coff)[M], int g0, int g1,
                                             float lb, float rb, const u64 (&qa)[Q][1 + d], const u64 (&qc)[M][Q][d],
                                             const float (&e)[M][Q], float (&cz)[M][Q], float (&cyz)[M][Q],
                                             float (&cxz)[M][Q]) {
@@ -167,10 +169,10 @@ __device__ __forceinline__ int bcount_range(const float* __restrict__ s, const i
     int n = 0;
 #pragma unroll 1
     for (int j = g0; j < g1; ++j) {
-        if (s[ldt + 4 * j] >= rb) break;
-        if (s[ldt + 4 * j + 3] <= lb) continue;
+        if (group_key_lo<DA>(s, j) >= rb) break;
+        if (group_key_hi<DA>(s, j) <= lb) continue;
         ulonglong2 ra[DA];
-        load_refs4<DA>(s, ldt, j, ra);
+        load_refs4<DA>(s, j, ra);
         // a: signed dy_t (compared through |.|), b: max |dy-| (or the signed single coordinate)
         float va[Q][4], vb[Q][4];
 #pragma unroll
@@ -187,7 +189,7 @@ __device__ __forceinline__ int bcount_range(const float* __restrict__ s, const i
 #pragma unroll
         for (int m = 0; m < M; ++m) {
             ulonglong2 rc[d];
-            load_refs4<d>(s + coff[m], ldt, j, rc);
+            load_refs4<d>(s + coff[m], j, rc);
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
                 float cc[4][d];
@@ -219,16 +221,17 @@ __device__ __forceinline__ int bcount_range(const float* __restrict__ s, const i
 // partial sum per member (its part wb) and the members' optional per-point outputs.
 template <int d, int Q, int KS, int M>
 __device__ __forceinline__ void bundle_warp_block(const BatchArgs& a, const InstDesc& L, const int32_t* mem, int nb,
-                                                  const float* sm, int ldt, int wb) {
+                                                  const float* sm, int wb) {
     constexpr int DA = 1 + d;
     constexpr int D = 1 + 2 * d;
     const int N = L.N;
     const int lane = threadIdx.x & 31;
     const int32_t* sidx = a.sorted_idx + L.sort_off;
     const int wbase = wb * 32 * Q;
-    int coff[M];  // offset of member m's source columns (ragged bundles repeat the last member)
+    const int ng = (N + 3) >> 2;
+    int coff[M];  // offset of member m's source tile (ragged bundles repeat the last member)
 #pragma unroll
-    for (int m = 0; m < M; ++m) coff[m] = (DA + min(m, nb - 1) * d) * ldt;
+    for (int m = 0; m < M; ++m) coff[m] = ng * 4 * (DA + min(m, nb - 1) * d);
     u64 qa[Q][DA];
     u64 qc[M][Q][d];
     float qkey[Q];
@@ -241,16 +244,15 @@ __device__ __forceinline__ void bundle_warp_block(const BatchArgs& a, const Inst
         qv[q] = pos < N;
         qidx[q] = qv[q] ? __ldg(sidx + pos) : -1;
 #pragma unroll
-        for (int c = 0; c < DA; ++c) qa[q][c] = dup2(qv[q] ? sm[c * ldt + pos] : 0.0f);
+        for (int c = 0; c < DA; ++c) qa[q][c] = dup2(qv[q] ? sm[tile_index<DA>(c, pos)] : 0.0f);
 #pragma unroll
         for (int m = 0; m < M; ++m)
 #pragma unroll
             for (int c = 0; c < d; ++c)
-                qc[m][q][c] = dup2(qv[q] ? sm[coff[m] + c * ldt + pos] : 0.0f);
-        qkey[q] = qv[q] ? sm[ldt + pos] : 0.0f;
+                qc[m][q][c] = dup2(qv[q] ? sm[coff[m] + tile_index<d>(c, pos)] : 0.0f);
+        qkey[q] = qv[q] ? sm[tile_index<DA>(1, pos)] : 0.0f;
         nvalid += __popc(__ballot_sync(0xffffffffu, qv[q]));
     }
-    const int ng = (N + 3) >> 2;
     unsigned long long groups_done = 0;
 
     // ---- pass 1: own block, then right, then left (radii: largest over the members)
@@ -263,9 +265,9 @@ __device__ __forceinline__ void bundle_warp_block(const BatchArgs& a, const Inst
             for (int s = 0; s < KS; ++s) t[m][q][s] = f_inf();
     const int g_own0 = wbase >> 2;
     const int g_own1 = min(ng, (min(wbase + 32 * Q, N) + 3) >> 2);
-    groups_done += bknn_range<d, Q, KS, M>(sm, coff, ldt, g_own0, g_own1, 0, qa, qc, qkey, qv, t);
-    groups_done += bknn_range<d, Q, KS, M>(sm, coff, ldt, g_own1, ng, +1, qa, qc, qkey, qv, t);
-    groups_done += bknn_range<d, Q, KS, M>(sm, coff, ldt, 0, g_own0, -1, qa, qc, qkey, qv, t);
+    groups_done += bknn_range<d, Q, KS, M>(sm, coff, g_own0, g_own1, 0, qa, qc, qkey, qv, t);
+    groups_done += bknn_range<d, Q, KS, M>(sm, coff, g_own1, ng, +1, qa, qc, qkey, qv, t);
+    groups_done += bknn_range<d, Q, KS, M>(sm, coff, 0, g_own0, -1, qa, qc, qkey, qv, t);
     float e[M][Q], emax[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -285,8 +287,8 @@ __device__ __forceinline__ void bundle_warp_block(const BatchArgs& a, const Inst
         for (int q = 0; q < Q; ++q) cz[m][q] = cyz[m][q] = cxz[m][q] = 0.0f;
     float lb, rb;
     warp_window(qkey, qv, emax, lb, rb);
-    const int g_lo = smem_first_greater(sm + ldt, N, lb) >> 2;
-    groups_done += bcount_range<d, Q, M>(sm, coff, ldt, g_lo, ng, lb, rb, qa, qc, e, cz, cyz, cxz);
+    const int g_lo = smem_first_greater<DA>(sm, N, lb) >> 2;
+    groups_done += bcount_range<d, Q, M>(sm, coff, g_lo, ng, lb, rb, qa, qc, e, cz, cyz, cxz);
 
     // ---- per member: digamma terms of Eq. 9 (compensated FP32), outputs at the original index
 #pragma unroll
@@ -361,8 +363,7 @@ __global__ void __launch_bounds__(kBundleThreads, d <= 3 ? 3 : 2) bundle_kernel(
         const InstDesc L = a.insts[w.inst];
         const int32_t* mem = a.members + L.bundle_off;
         const int nb = L.bundle_n;
-        const int ldt = (L.N + 3) & ~3;
-        stage_bundle<d, M>(a, L, mem, nb, a.sorted_idx + L.sort_off, ldt, sm);
+        stage_bundle<d, M>(a, L, mem, nb, a.sorted_idx + L.sort_off, sm);
         if (threadIdx.x == 0) s_wblock = w.q0;
         __syncthreads();
         const int wb1 = min((L.N + 32 * Q - 1) / (32 * Q), w.q0 + L.wb_chunk);
@@ -371,7 +372,7 @@ __global__ void __launch_bounds__(kBundleThreads, d <= 3 ? 3 : 2) bundle_kernel(
             if ((threadIdx.x & 31) == 0) wb = atomicAdd(&s_wblock, 1);
             wb = __shfl_sync(0xffffffffu, wb, 0);
             if (wb >= wb1) break;
-            bundle_warp_block<d, Q, KS, M>(a, L, mem, nb, sm, ldt, wb);
+            bundle_warp_block<d, Q, KS, M>(a, L, mem, nb, sm, wb);
         }
     }
 }

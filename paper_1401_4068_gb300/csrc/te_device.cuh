@@ -102,10 +102,33 @@ __device__ __forceinline__ void diff4(const u64 (&qq)[D], const ulonglong2 (&r)[
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Shared-memory tiles hold points in groups of four: group g (points 4g .. 4g+3) stores its
+// D coordinates x 4 points contiguously, coordinate c of point p at
+//   s[((p >> 2) * D + c) * 4 + (p & 3)],
+// so one 128-bit broadcast load reads coordinate c of a whole group at the constant offset 16c
+// bytes from the group's base (one address per group instead of one per coordinate).
+// ---------------------------------------------------------------------------------------
 template <int D>
-__device__ __forceinline__ void load_refs4(const float* __restrict__ s, int ldt, int j, ulonglong2 (&r)[D]) {
+__device__ __forceinline__ int tile_index(int c, int p) {
+    return ((p >> 2) * D + c) * 4 + (p & 3);
+}
+
+template <int D>
+__device__ __forceinline__ void load_refs4(const float* __restrict__ s, int j, ulonglong2 (&r)[D]) {
+    const float* g = s + j * (4 * D);
 #pragma unroll
-    for (int c = 0; c < D; ++c) r[c] = *reinterpret_cast<const ulonglong2*>(s + c * ldt + 4 * j);
+    for (int c = 0; c < D; ++c) r[c] = *reinterpret_cast<const ulonglong2*>(g + 4 * c);
+}
+
+// smallest / largest key (coordinate 1) of group j of a tile (groups are in key order in the sweep)
+template <int D>
+__device__ __forceinline__ float group_key_lo(const float* __restrict__ s, int j) {
+    return s[(j * D + 1) * 4];
+}
+template <int D>
+__device__ __forceinline__ float group_key_hi(const float* __restrict__ s, int j) {
+    return s[(j * D + 1) * 4 + 3];
 }
 
 // Pass-1 step for four references against the thread's Q queries. For D >= 5 every distance
@@ -142,18 +165,17 @@ __device__ __forceinline__ void knn_step4(const u64 (&qq)[Q][D], const ulonglong
 }
 
 // ---------------------------------------------------------------------------------------
-// Pass 1 over one staged reference tile: smem holds coordinate c of reference j at
-// s[c * ldt + j] (structure of arrays, +inf past the last valid reference). Every thread
-// streams the whole tile against its Q register-resident queries; four references are
-// read per 128-bit broadcast load.
+// Pass 1 over one staged reference tile (grouped layout above, +inf past the last valid
+// reference). Every thread streams the whole tile against its Q register-resident queries;
+// four references are read per 128-bit broadcast load.
 // ---------------------------------------------------------------------------------------
 template <int D, int Q, int KS>
-__device__ __forceinline__ void knn_tile(const float* __restrict__ s, int ldt, int n4,
-                                         const u64 (&qq)[Q][D], float (&t)[Q][KS]) {
+__device__ __forceinline__ void knn_tile(const float* __restrict__ s, int n4, const u64 (&qq)[Q][D],
+                                         float (&t)[Q][KS]) {
 #pragma unroll 1
     for (int j = 0; j < n4; ++j) {
         ulonglong2 r[D];
-        load_refs4<D>(s, ldt, j, r);
+        load_refs4<D>(s, j, r);
         knn_step4<D, Q, KS>(qq, r, t);
     }
 }
@@ -181,14 +203,14 @@ __device__ __forceinline__ void count_one(const float (&d)[1 + DY + DX], float e
 }
 
 template <int DY, int DX, int Q>
-__device__ __forceinline__ void count_tile(const float* __restrict__ s, int ldt, int n4,
-                                           const u64 (&qq)[Q][1 + DY + DX], const float (&e)[Q],
-                                           float (&cz)[Q], float (&cyz)[Q], float (&cxz)[Q]) {
+__device__ __forceinline__ void count_tile(const float* __restrict__ s, int n4, const u64 (&qq)[Q][1 + DY + DX],
+                                           const float (&e)[Q], float (&cz)[Q], float (&cyz)[Q],
+                                           float (&cxz)[Q]) {
     constexpr int D = 1 + DY + DX;
 #pragma unroll 1
     for (int j = 0; j < n4; ++j) {
         ulonglong2 r[D];
-        load_refs4<D>(s, ldt, j, r);
+        load_refs4<D>(s, j, r);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             float dx[D], dy[D], dz[D], dw[D];

@@ -51,7 +51,7 @@ __device__ __forceinline__ void block_minmax(float& a, float& b, float* sb) {
 
 template <int d>
 __device__ __forceinline__ void stage_tile_sorted(const InstDesc& I, const int32_t* __restrict__ sidx, int base,
-                                                  int nv, int ldt, float* sm, int32_t* flags) {
+                                                  int nv, float* sm, int32_t* flags) {
     constexpr int D = 1 + 2 * d;
     const int nfill = (nv + 3) & ~3;
     for (int p = threadIdx.x; p < nfill; p += blockDim.x) {
@@ -63,7 +63,7 @@ __device__ __forceinline__ void stage_tile_sorted(const InstDesc& I, const int32
             for (int c = 0; c < D; ++c) v[c] = f_inf();
         }
 #pragma unroll
-        for (int c = 0; c < D; ++c) sm[c * ldt + p] = v[c];
+        for (int c = 0; c < D; ++c) sm[tile_index<D>(c, p)] = v[c];
     }
 }
 
@@ -91,10 +91,10 @@ __device__ __forceinline__ void current_radii(const float (&t)[Q][KS], float (&r
 
 // one group of four references (group j of the staged tile) against the warp's queries, pass 1
 template <int D, int Q, int KS>
-__device__ __forceinline__ void knn_group(const float* __restrict__ s, int ldt, int j, const u64 (&qq)[Q][D],
+__device__ __forceinline__ void knn_group(const float* __restrict__ s, int j, const u64 (&qq)[Q][D],
                                           float (&t)[Q][KS]) {
     ulonglong2 r[D];
-    load_refs4<D>(s, ldt, j, r);
+    load_refs4<D>(s, j, r);
     knn_step4<D, Q, KS>(qq, r, t);
 }
 
@@ -103,7 +103,7 @@ __device__ __forceinline__ void knn_group(const float* __restrict__ s, int ldt, 
 // window, dir -1 descends and stops at the first group whose largest key is left of it.
 // Returns the number of groups evaluated; sets `done` when it stopped at a window edge.
 template <int D, int Q, int KS>
-__device__ __forceinline__ int knn_range(const float* __restrict__ s, int ldt, int g0, int g1, int dir,
+__device__ __forceinline__ int knn_range(const float* __restrict__ s, int g0, int g1, int dir,
                                          const u64 (&qq)[Q][D], const float (&qkey)[Q], const bool (&qv)[Q],
                                          float (&t)[Q][KS], bool& done) {
     float r[Q], lb, rb;
@@ -113,15 +113,15 @@ __device__ __forceinline__ int knn_range(const float* __restrict__ s, int ldt, i
 #pragma unroll 1
     for (int jj = g0; jj < g1; ++jj) {
         const int j = dir < 0 ? g1 - 1 - (jj - g0) : jj;
-        if (dir > 0 && s[ldt + 4 * j] >= rb) {
+        if (dir > 0 && group_key_lo<D>(s, j) >= rb) {
             done = true;
             break;
         }
-        if (dir < 0 && s[ldt + 4 * j + 3] <= lb) {
+        if (dir < 0 && group_key_hi<D>(s, j) <= lb) {
             done = true;
             break;
         }
-        knn_group<D, Q, KS>(s, ldt, j, qq, t);
+        knn_group<D, Q, KS>(s, j, qq, t);
         if ((++n & 3) == 0 && dir != 0) {
             current_radii(t, r);
             warp_window(qkey, qv, r, lb, rb);
@@ -133,17 +133,17 @@ __device__ __forceinline__ int knn_range(const float* __restrict__ s, int ldt, i
 // pass 2 over groups [g0, g1) ascending, skipping groups left of the window [lb, rb] and
 // stopping at the first group right of it
 template <int DY, int DX, int Q>
-__device__ __forceinline__ int count_range(const float* __restrict__ s, int ldt, int g0, int g1, float lb, float rb,
+__device__ __forceinline__ int count_range(const float* __restrict__ s, int g0, int g1, float lb, float rb,
                                            const u64 (&qq)[Q][1 + DY + DX], const float (&e)[Q], float (&cz)[Q],
                                            float (&cyz)[Q], float (&cxz)[Q]) {
     constexpr int D = 1 + DY + DX;
     int n = 0;
 #pragma unroll 1
     for (int j = g0; j < g1; ++j) {
-        if (s[ldt + 4 * j] >= rb) break;
-        if (s[ldt + 4 * j + 3] <= lb) continue;
+        if (group_key_lo<D>(s, j) >= rb) break;
+        if (group_key_hi<D>(s, j) <= lb) continue;
         ulonglong2 r[D];
-        load_refs4<D>(s, ldt, j, r);
+        load_refs4<D>(s, j, r);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             float dx[D], dy[D], dz[D], dw[D];
@@ -229,7 +229,7 @@ __device__ __forceinline__ void process_item_sweep(const BatchArgs& a, const Ins
         if (staged == ti) return;
         const int base = ti * ldt;
         __syncthreads();
-        stage_tile_sorted<d>(I, sidx, base, min(ldt, N - base), ldt, sm, a.flags);
+        stage_tile_sorted<d>(I, sidx, base, min(ldt, N - base), sm, a.flags);
         __syncthreads();
         staged = ti;
     };
@@ -246,10 +246,10 @@ __device__ __forceinline__ void process_item_sweep(const BatchArgs& a, const Ins
     if (warp_active) {
         const int g_own0 = (wbase - ctile * ldt) >> 2;
         const int g_own1 = min(ngroups(ctile), (min(wbase + 32 * Q, N) - ctile * ldt + 3) >> 2);
-        groups_done += knn_range<D, Q, KS>(sm, ldt, g_own0, g_own1, 0, qq, qkey, qv, t, rdone);
+        groups_done += knn_range<D, Q, KS>(sm, g_own0, g_own1, 0, qq, qkey, qv, t, rdone);
         rdone = false;
-        groups_done += knn_range<D, Q, KS>(sm, ldt, g_own1, ngroups(ctile), +1, qq, qkey, qv, t, rdone);
-        groups_done += knn_range<D, Q, KS>(sm, ldt, 0, g_own0, -1, qq, qkey, qv, t, ldone);
+        groups_done += knn_range<D, Q, KS>(sm, g_own1, ngroups(ctile), +1, qq, qkey, qv, t, rdone);
+        groups_done += knn_range<D, Q, KS>(sm, 0, g_own0, -1, qq, qkey, qv, t, ldone);
     }
     for (int ti = ctile + 1; ti < ntile; ++ti) {  // right tiles
         float r[Q], lb, rb;
@@ -260,7 +260,7 @@ __device__ __forceinline__ void process_item_sweep(const BatchArgs& a, const Ins
         if (!(__ldg(skey + ti * ldt) < brb)) break;
         stage(ti);
         if (warp_active && !rdone)
-            groups_done += knn_range<D, Q, KS>(sm, ldt, 0, ngroups(ti), +1, qq, qkey, qv, t, rdone);
+            groups_done += knn_range<D, Q, KS>(sm, 0, ngroups(ti), +1, qq, qkey, qv, t, rdone);
     }
     for (int ti = ctile - 1; ti >= 0; --ti) {  // left tiles
         float r[Q], lb, rb;
@@ -271,7 +271,7 @@ __device__ __forceinline__ void process_item_sweep(const BatchArgs& a, const Ins
         if (!(__ldg(skey + (ti + 1) * ldt - 1) > blb)) break;
         stage(ti);
         if (warp_active && !ldone)
-            groups_done += knn_range<D, Q, KS>(sm, ldt, 0, ngroups(ti), -1, qq, qkey, qv, t, ldone);
+            groups_done += knn_range<D, Q, KS>(sm, 0, ngroups(ti), -1, qq, qkey, qv, t, ldone);
     }
     float e[Q];
 #pragma unroll
@@ -291,7 +291,7 @@ __device__ __forceinline__ void process_item_sweep(const BatchArgs& a, const Ins
         for (int ti = plo / ldt; ti <= (phi - 1) / ldt; ++ti) {
             stage(ti);
             if (warp_active)
-                groups_done += count_range<d, d, Q>(sm, ldt, 0, ngroups(ti), lb, rb, qq, e, cz, cyz, cxz);
+                groups_done += count_range<d, d, Q>(sm, 0, ngroups(ti), lb, rb, qq, e, cz, cyz, cxz);
         }
     }
 
@@ -334,12 +334,13 @@ __device__ __forceinline__ void process_item_sweep(const BatchArgs& a, const Ins
     }
 }
 
-// first position p in [0, n) of the shared-memory key row with key > x (keys ascending)
-__device__ __forceinline__ int smem_first_greater(const float* __restrict__ key, int n, float x) {
+// first position p in [0, n) of a staged tile whose key (coordinate 1) is > x (keys ascending)
+template <int D>
+__device__ __forceinline__ int smem_first_greater(const float* __restrict__ s, int n, float x) {
     int lo = 0, hi = n;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (key[mid] > x) hi = mid;
+        if (s[tile_index<D>(1, mid)] > x) hi = mid;
         else lo = mid + 1;
     }
     return lo;
@@ -349,8 +350,8 @@ __device__ __forceinline__ int smem_first_greater(const float* __restrict__ key,
 // memory: pass 1 (own block, then right, then left), pass 2 over the key window, digamma terms;
 // the block's partial sum is written to part. No CTA-wide barrier.
 template <int d, int Q, int KS>
-__device__ __forceinline__ void sweep_warp_block(const BatchArgs& a, const InstDesc& I, const float* sm, int ldt,
-                                                 int wb, int part) {
+__device__ __forceinline__ void sweep_warp_block(const BatchArgs& a, const InstDesc& I, const float* sm, int wb,
+                                                 int part) {
     constexpr int D = 1 + 2 * d;
     const int N = I.N;
     const int lane = threadIdx.x & 31;
@@ -368,8 +369,8 @@ __device__ __forceinline__ void sweep_warp_block(const BatchArgs& a, const InstD
         qidx[q] = qv[q] ? __ldg(sidx + pos) : -1;
         // the staged tile holds the sorted points: read the query's coordinates from it
 #pragma unroll
-        for (int c = 0; c < D; ++c) qq[q][c] = dup2(qv[q] ? sm[c * ldt + pos] : 0.0f);
-        qkey[q] = qv[q] ? sm[ldt + pos] : 0.0f;
+        for (int c = 0; c < D; ++c) qq[q][c] = dup2(qv[q] ? sm[tile_index<D>(c, pos)] : 0.0f);
+        qkey[q] = qv[q] ? sm[tile_index<D>(1, pos)] : 0.0f;
         nvalid += __popc(__ballot_sync(0xffffffffu, qv[q]));
     }
     const int ng = (N + 3) >> 2;
@@ -382,9 +383,9 @@ __device__ __forceinline__ void sweep_warp_block(const BatchArgs& a, const InstD
     bool done = false;
     const int g_own0 = wbase >> 2;
     const int g_own1 = min(ng, (min(wbase + 32 * Q, N) + 3) >> 2);
-    groups_done += knn_range<D, Q, KS>(sm, ldt, g_own0, g_own1, 0, qq, qkey, qv, t, done);
-    groups_done += knn_range<D, Q, KS>(sm, ldt, g_own1, ng, +1, qq, qkey, qv, t, done);
-    groups_done += knn_range<D, Q, KS>(sm, ldt, 0, g_own0, -1, qq, qkey, qv, t, done);
+    groups_done += knn_range<D, Q, KS>(sm, g_own0, g_own1, 0, qq, qkey, qv, t, done);
+    groups_done += knn_range<D, Q, KS>(sm, g_own1, ng, +1, qq, qkey, qv, t, done);
+    groups_done += knn_range<D, Q, KS>(sm, 0, g_own0, -1, qq, qkey, qv, t, done);
     float e[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) e[q] = topk_select(t[q], a.k);
@@ -394,8 +395,8 @@ __device__ __forceinline__ void sweep_warp_block(const BatchArgs& a, const InstD
     for (int q = 0; q < Q; ++q) cz[q] = cyz[q] = cxz[q] = 0.0f;
     float lb, rb;
     warp_window(qkey, qv, e, lb, rb);
-    const int g_lo = smem_first_greater(sm + ldt, N, lb) >> 2;
-    groups_done += count_range<d, d, Q>(sm, ldt, g_lo, ng, lb, rb, qq, e, cz, cyz, cxz);
+    const int g_lo = smem_first_greater<D>(sm, N, lb) >> 2;
+    groups_done += count_range<d, d, Q>(sm, g_lo, ng, lb, rb, qq, e, cz, cyz, cxz);
 
     FF acc{0.0f, 0.0f};
     float acc_abs = 0.0f;
@@ -447,9 +448,8 @@ __device__ __forceinline__ void process_instance_sweep_warps(const BatchArgs& a,
                                                              float* sm, int* s_wblock) {
     constexpr int D = 1 + 2 * d;
     const int N = I.N;
-    const int ldt = (N + 3) & ~3;
     const int32_t* sidx = a.sorted_idx + I.sort_off;
-    stage_tile_sorted<d>(I, sidx, 0, N, ldt, sm, a.flags);
+    stage_tile_sorted<d>(I, sidx, 0, N, sm, a.flags);
     if (threadIdx.x == 0) *s_wblock = wb0;
     __syncthreads();
     const int wb1 = min((N + 32 * Q - 1) / (32 * Q), wb0 + I.wb_chunk);  // this item's warp blocks
@@ -458,7 +458,7 @@ __device__ __forceinline__ void process_instance_sweep_warps(const BatchArgs& a,
         if ((threadIdx.x & 31) == 0) wb = atomicAdd(s_wblock, 1);
         wb = __shfl_sync(0xffffffffu, wb, 0);
         if (wb >= wb1) break;
-        sweep_warp_block<d, Q, KS>(a, I, sm, ldt, wb, I.part_begin + wb);
+        sweep_warp_block<d, Q, KS>(a, I, sm, wb, I.part_begin + wb);
     }
     __syncthreads();  // the staged instance stays until every warp is done with it
     (void)D;

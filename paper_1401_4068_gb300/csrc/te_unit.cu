@@ -43,14 +43,15 @@ __global__ void embed_kernel(const float* __restrict__ src, const float* __restr
     for (int m = 0; m < d; ++m) points[(size_t)(1 + d + m) * ld + i] = x[t - u - m * tau];
 }
 
-// stage references base .. base+ldt-1 of an SoA point array into smem, +inf past N
+// stage references base .. base+kUnitTile-1 of an SoA point array into a shared-memory tile
+// (groups of four points, te_device.cuh), +inf past N
 template <int D>
 __device__ __forceinline__ void stage_soa(const float* __restrict__ pts, int ld, int N, int base,
                                           float* s) {
     for (int p = threadIdx.x; p < kUnitTile; p += blockDim.x) {
         const bool ok = base + p < N;
 #pragma unroll
-        for (int c = 0; c < D; ++c) s[c * kUnitTile + p] = ok ? pts[(size_t)c * ld + base + p] : f_inf();
+        for (int c = 0; c < D; ++c) s[tile_index<D>(c, p)] = ok ? pts[(size_t)c * ld + base + p] : f_inf();
     }
 }
 
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(kUnitThreads) knn_exact_kernel(const float* __
         stage_soa<D>(pts, ld, N, base, s);
         __syncthreads();
         const int nv = min(kUnitTile, N - base);
-        knn_tile<D, kUnitQ, KS>(s, kUnitTile, (nv + 3) >> 2, qq, t);
+        knn_tile<D, kUnitQ, KS>(s, (nv + 3) >> 2, qq, t);
     }
 #pragma unroll
     for (int q = 0; q < kUnitQ; ++q) {
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(kUnitThreads) count_exact_kernel(const float* 
         stage_soa<D>(pts, ld, N, base, s);
         __syncthreads();
         const int nv = min(kUnitTile, N - base);
-        count_tile<DY, DX, kUnitQ>(s, kUnitTile, (nv + 3) >> 2, qq, e, cz, cyz, cxz);
+        count_tile<DY, DX, kUnitQ>(s, (nv + 3) >> 2, qq, e, cz, cyz, cxz);
     }
 #pragma unroll
     for (int q = 0; q < kUnitQ; ++q) {

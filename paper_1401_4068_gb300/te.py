@@ -182,7 +182,7 @@ def te_embed(h: Handle, src: torch.Tensor, tgt: torch.Tensor, d: int, tau: int, 
     D = 1 + 2 * d
     ld = ld or ((N + 3) // 4) * 4
     if points is None:
-        points = torch.empty((D, ld), dtype=torch.float32, device=src.device)
+        points = torch.full((D, ld), float("nan"), dtype=torch.float32, device=src.device)
     _need(points, torch.float32, "points")
     if perm is not None:
         _need(perm, torch.int32, "perm")
@@ -196,8 +196,8 @@ def te_knn_maxnorm(h: Handle, points: torch.Tensor, N: int, D: int, ld: int, k: 
                    eps: Optional[torch.Tensor] = None, want_nn: bool = False, stream=None):
     _need(points, torch.float32, "points")
     if eps is None:
-        eps = torch.empty(N, dtype=torch.float32, device=points.device)
-    nn = torch.empty((N, k), dtype=torch.int32, device=points.device) if want_nn else None
+        eps = torch.full((N,), float("nan"), dtype=torch.float32, device=points.device)
+    nn = torch.full((N, k), -1, dtype=torch.int32, device=points.device) if want_nn else None
     h.check(h.lib.te_knn_maxnorm(h.h, _ptr(points), N, D, ld, k, _ptr(eps), _ptr(nn),
                                  _stream(stream)))
     return (eps, nn) if want_nn else eps
@@ -208,7 +208,7 @@ def te_range_count(h: Handle, points: torch.Tensor, N: int, d_y: int, d_x: int, 
     _need(points, torch.float32, "points")
     _need(eps, torch.float32, "eps")
     if counts is None:
-        counts = torch.empty((3, N), dtype=torch.int32, device=points.device)
+        counts = torch.full((3, N), -1, dtype=torch.int32, device=points.device)
     h.check(h.lib.te_range_count(h.h, _ptr(points), N, d_y, d_x, ld, _ptr(eps), _ptr(counts),
                                  _stream(stream)))
     return counts
@@ -270,10 +270,11 @@ def te_estimate(h: Handle, series: Sequence[DeviceSeries], instances: Sequence, 
         if 0 <= int(it.series) < len(series):  # the library validates the rest
             npts += series[int(it.series)].src.shape[0] * int(it.window)
     if te is None:
-        te = torch.empty(n, dtype=torch.float64, device=dev)
-    err = torch.empty(n, dtype=torch.float64, device=dev) if want_err else None
-    counts = torch.empty(3 * npts, dtype=torch.int32, device=dev) if want_counts else None
-    eps = torch.empty(npts, dtype=torch.float32, device=dev) if want_counts else None
+        te = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
+    err = torch.full((n,), float("nan"), dtype=torch.float64, device=dev) if want_err else None
+    # sentinels (-1, NaN): a point the library failed to write can never pass for a result
+    counts = torch.full((3 * npts,), -1, dtype=torch.int32, device=dev) if want_counts else None
+    eps = torch.full((npts,), float("nan"), dtype=torch.float32, device=dev) if want_counts else None
     h.check(h.lib.te_estimate(h.h, ser, len(series), ins, n, int(k), _ptr(te), _ptr(err),
                               _ptr(counts), _ptr(eps), _stream(stream)))
     if not (want_err or want_counts):
@@ -289,9 +290,9 @@ def te_surrogate_test(h: Handle, series: Sequence[DeviceSeries], t_starts: Seque
     ser = _series_array(series)
     ts = (C.c_int32 * max(1, nt))(*[int(t) for t in t_starts])
     if out is None:
-        out = {"te_orig": torch.empty((ns, nt), dtype=torch.float64, device=dev),
-               "te_surr": torch.empty((ns, nt, max(S, 1)), dtype=torch.float64, device=dev),
-               "p": torch.empty((ns, nt), dtype=torch.float64, device=dev)}
+        out = {"te_orig": torch.full((ns, nt), float("nan"), dtype=torch.float64, device=dev),
+               "te_surr": torch.full((ns, nt, max(S, 1)), float("nan"), dtype=torch.float64, device=dev),
+               "p": torch.full((ns, nt), float("nan"), dtype=torch.float64, device=dev)}
     h.check(h.lib.te_surrogate_test(h.h, ser, ns, C.cast(ts, C.c_void_p), nt, int(window),
                                     int(S), int(k), _ptr(out["te_orig"]), _ptr(out["te_surr"]),
                                     _ptr(out["p"]), _stream(stream)))
@@ -344,9 +345,9 @@ def te_delay_scan(h: Handle, series: DeviceSeries, t_starts: Sequence[int], wind
     ser = _series_array([series])
     ts = (C.c_int32 * max(1, n_t))(*[int(t) for t in t_starts])
     if out is None:  # sizes clamped to >= 1 so that the library, not torch, rejects bad ranges
-        out = {"te": torch.empty((max(n_u, 1), max(n_t, 1)), dtype=torch.float64, device=dev),
-               "p": torch.empty((max(n_u, 1), max(n_t, 1)), dtype=torch.float64, device=dev),
-               "u_best": torch.empty(max(n_t, 1), dtype=torch.int32, device=dev)}
+        out = {"te": torch.full((max(n_u, 1), max(n_t, 1)), float("nan"), dtype=torch.float64, device=dev),
+               "p": torch.full((max(n_u, 1), max(n_t, 1)), float("nan"), dtype=torch.float64, device=dev),
+               "u_best": torch.full((max(n_t, 1),), -1, dtype=torch.int32, device=dev)}
     h.check(h.lib.te_delay_scan(h.h, ser, C.cast(ts, C.c_void_p), n_t, int(window), int(u_lo), int(u_hi),
                                 int(S), int(k), _ptr(out["te"]), _ptr(out["p"]), _ptr(out["u_best"]),
                                 _stream(stream)))

@@ -121,7 +121,7 @@ def test_surrogate_test_two_series_and_zero_surrogates(te_handle):
     assert torch.isnan(out0["p"]).all()
 
 
-@pytest.mark.parametrize("threads,qpt", [(64, 2), (96, 4), (160, 4), (256, 2), (512, 4), (0, 0)])
+@pytest.mark.parametrize("threads,qpt", [(64, 2), (96, 4), (160, 4), (256, 2), (512, 4), (1024, 2), (640, 1), (0, 0)])
 def test_launch_shape_does_not_change_counts(te_handle, threads, qpt):
     w = I.config(4, n_pairs=6, n_t=3)
     ds = te.to_device(w.series)
