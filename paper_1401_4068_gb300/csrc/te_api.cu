@@ -116,10 +116,10 @@ struct Plan {
     double err_coef = 0;
     int64_t n_points = 0;
     // bundle kernel (target-part sharing): its work items, member lists, d and launch shape
-    std::vector<WorkItem> bitems;
+    std::vector<WorkItem> bitems;  // resident bundles' items first (n_bres), then tiled bundles'
     std::vector<int32_t> members;
-    int bd = 0, bgrid = 0, n_bundled = 0;
-    size_t bsmem = 0;
+    int bd = 0, bgrid = 0, tgrid = 0, n_bundled = 0, n_bres = 0;
+    size_t bsmem = 0, tsmem = 0;   // dynamic shared memory of the resident / tiled bundle launches
     uint64_t table_hash = 0;  // of the device tables (instances, items, bundles): part of the graph key
 };
 
@@ -427,8 +427,12 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
     int max_parts = 1;
     int n_parts = 0;
     // target-part sharing: estimates with one target part (target series, repetitions, window
-    // start, window, d, tau) that fit shared memory together form bundles of up to kBundleMax
-    // (no bundle of one), processed by the bundle kernel; one embedding dimension per batch
+    // start, window, d, tau) form bundles of up to kBundleMax (no bundle of one), processed by the
+    // bundle kernel; one embedding dimension per batch. A bundle that fits kResidentMaxBytes is
+    // staged whole (warps take 32-query blocks); a larger one runs CTA tiles around blocks of
+    // kBundleThreads queries (tile budget: three CTAs per SM for d <= 3, two above), but only when
+    // its estimates would not be resident on their own either (a resident unshared estimate beats
+    // a tiled bundle: the AR(1) scan measured 317 ms unshared vs 450 ms tiled-bundled)
     std::vector<char> bundled(n_inst, 0);
     if (sweep && h->sharing && !h->per_instance && ks == 5) {
         std::map<std::tuple<const float*, int, int, int, int, int, int>, std::vector<int>> by_target;
@@ -436,32 +440,49 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
             const InstDesc& I = P->insts[i];
             by_target[std::make_tuple(I.tgt, I.T, I.R, I.t_start, I.W, I.d, I.tau)].push_back(i);
         }
-        int64_t shareable[kMaxBatchedD + 1] = {0};  // estimates in groups of >= 2 that fit, per d
+        auto resident_bytes = [](const InstDesc& I) {
+            return (int64_t)((I.N + 3) & ~3) * (1 + I.d + te::kBundleMax * I.d) * 4;
+        };
+        auto shares = [&](const InstDesc& I) {  // a bundle of I's group is staged whole or helps tiled
+            return resident_bytes(I) <= kResidentMaxBytes ||
+                   (int64_t)((I.N + 3) & ~3) * (1 + 2 * I.d) * 4 > kResidentMaxBytes;
+        };
+        int64_t shareable[kMaxBatchedD + 1] = {0};  // estimates in groups of >= 2 that share, per d
         for (const auto& kv : by_target)
-            if (kv.second.size() >= 2) {
-                const InstDesc& I = P->insts[kv.second[0]];
-                const int64_t bytes = (int64_t)((I.N + 3) & ~3) * (1 + I.d + te::kBundleMax * I.d) * 4;
-                if (bytes <= kResidentMaxBytes) shareable[I.d] += (int64_t)kv.second.size();
-            }
+            if (kv.second.size() >= 2 && shares(P->insts[kv.second[0]]))
+                shareable[P->insts[kv.second[0]].d] += (int64_t)kv.second.size();
         for (int d = 1; d <= kMaxBundleD; ++d)
             if (shareable[d] > (P->bd ? shareable[P->bd] : 0)) P->bd = d;
-        int n_bundles = 0;
+        int n_bundles = 0;  // resident ones, for their work split
         for (const auto& kv : by_target) {
             const InstDesc& I0 = P->insts[kv.second[0]];
-            const int64_t bytes = (int64_t)((I0.N + 3) & ~3) * (1 + I0.d + te::kBundleMax * I0.d) * 4;
-            if (kv.second.size() < 2 || I0.d != P->bd || bytes > kResidentMaxBytes) continue;
-            P->bsmem = std::max(P->bsmem, (size_t)bytes);
-            n_bundles += (int)((kv.second.size() + te::kBundleMax - 1) / te::kBundleMax);
+            if (kv.second.size() < 2 || I0.d != P->bd || !shares(I0)) continue;
+            if (resident_bytes(I0) <= kResidentMaxBytes) {
+                P->bsmem = std::max(P->bsmem, (size_t)resident_bytes(I0));
+                n_bundles += (int)((kv.second.size() + te::kBundleMax - 1) / te::kBundleMax);
+            }
         }
         const int per_b = 32 * te::kBundleQ;
+        const int blockq = te::kBundleThreads * te::kBundleQ;
+        std::vector<WorkItem> titems;
         for (const auto& kv : by_target) {
             const std::vector<int>& v = kv.second;
             const InstDesc& I0 = P->insts[v[0]];
-            const int64_t bytes = (int64_t)((I0.N + 3) & ~3) * (1 + I0.d + te::kBundleMax * I0.d) * 4;
-            if (v.size() < 2 || I0.d != P->bd || bytes > kResidentMaxBytes) continue;
-            const int nwb = (I0.N + per_b - 1) / per_b;
-            const int split = std::max(1, std::min(nwb, (want_items + n_bundles - 1) / std::max(1, n_bundles)));
-            const int chunk = (nwb + split - 1) / split;
+            if (v.size() < 2 || I0.d != P->bd || !shares(I0)) continue;
+            const bool resident = resident_bytes(I0) <= kResidentMaxBytes;
+            int nparts_b, chunk = 0;
+            if (resident) {
+                const int nwb = (I0.N + per_b - 1) / per_b;
+                const int split = std::max(1, std::min(nwb, (want_items + n_bundles - 1) / std::max(1, n_bundles)));
+                chunk = (nwb + split - 1) / split;
+                nparts_b = nwb;
+            } else {
+                const int cols = 1 + I0.d + te::kBundleMax * I0.d;
+                const int budget = I0.d <= 3 ? 72 * 1024 : 110 * 1024;
+                const int cap = std::max(blockq, (budget / (cols * 4)) / blockq * blockq);
+                P->tsmem = std::max(P->tsmem, (size_t)cap * cols * 4);
+                nparts_b = (I0.N + blockq - 1) / blockq;
+            }
             size_t pos = 0;
             while (pos < v.size()) {
                 size_t nb = std::min<size_t>(te::kBundleMax, v.size() - pos);
@@ -475,19 +496,25 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
                     InstDesc& I = P->insts[i];
                     P->members.push_back(i);
                     bundled[i] = 1;
-                    I.warp_mode = 1;
+                    I.warp_mode = resident ? 1 : 0;
                     I.item_begin = 0;
                     I.n_items = 0;
                     I.part_begin = n_parts;
-                    I.n_parts = nwb;
-                    n_parts += nwb;
-                    max_parts = std::max(max_parts, nwb);
+                    I.n_parts = nparts_b;
+                    n_parts += nparts_b;
+                    max_parts = std::max(max_parts, nparts_b);
                 }
-                for (int c = 0; c * chunk < nwb; ++c) P->bitems.push_back(WorkItem{v[pos], c * chunk});
+                if (resident) {
+                    for (int c = 0; c * chunk < nparts_b; ++c) P->bitems.push_back(WorkItem{v[pos], c * chunk});
+                } else {
+                    for (int c = 0; c < nparts_b; ++c) titems.push_back(WorkItem{v[pos], c * blockq});
+                }
                 pos += nb;
                 ++P->n_bundled;
             }
         }
+        P->n_bres = (int)P->bitems.size();
+        P->bitems.insert(P->bitems.end(), titems.begin(), titems.end());
     }
     for (int i : order) {
         if (bundled[i]) continue;
@@ -550,17 +577,19 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
     if (e != cudaSuccess) return h->cuda_fail(e, "occupancy query");
     if (per_sm < 1) return h->fail(TE_ENOTIMPL, "batched kernel does not fit: threads=%d smem=%zu", threads, P->smem);
     P->grid = (int)std::min<int64_t>((int64_t)per_sm * h->sm_count, (int64_t)P->items.size());
-    if (!P->bitems.empty()) {
-        const void* bf = te::bundle_kernel_ptr(P->bd, ks);
+    for (int tiled = 0; tiled < 2; ++tiled) {
+        const int64_t n = tiled ? (int64_t)P->bitems.size() - P->n_bres : (int64_t)P->n_bres;
+        if (n <= 0) continue;
+        const size_t smem = tiled ? P->tsmem : P->bsmem;
+        const void* bf = te::bundle_kernel_ptr(P->bd, ks, tiled != 0);
         if (!bf) return h->fail(TE_ENOTIMPL, "no bundle kernel for d=%d ks=%d", P->bd, ks);
-        if ((e = cudaFuncSetAttribute(bf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->bsmem)) != cudaSuccess)
+        if ((e = cudaFuncSetAttribute(bf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return h->cuda_fail(e, "cudaFuncSetAttribute (bundle)");
         int bper = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bper, bf, te::kBundleThreads, P->bsmem)) !=
-            cudaSuccess)
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bper, bf, te::kBundleThreads, smem)) != cudaSuccess)
             return h->cuda_fail(e, "occupancy query (bundle)");
-        if (bper < 1) return h->fail(TE_ENOTIMPL, "bundle kernel does not fit: smem=%zu", P->bsmem);
-        P->bgrid = (int)std::min<int64_t>((int64_t)bper * h->sm_count, (int64_t)P->bitems.size());
+        if (bper < 1) return h->fail(TE_ENOTIMPL, "bundle kernel does not fit: smem=%zu", smem);
+        (tiled ? P->tgrid : P->bgrid) = (int)std::min<int64_t>((int64_t)bper * h->sm_count, n);
     }
     uint64_t th = 1469598103934665603ull;
     th = fnv(th, P->insts.data(), P->insts.size() * sizeof(InstDesc));
@@ -683,7 +712,7 @@ te_status run_per_instance(te_handle* h, const Plan& P, int n_inst, int k, doubl
     te_status st = upload_tables(h, P, stream);
     if (st != TE_OK) return st;
     h->drop_graph();
-    cudaError_t e = cudaMemsetAsync(h->d_words.p + 3, 0, (size_t)n_inst * sizeof(int32_t), stream);
+    cudaError_t e = cudaMemsetAsync(h->d_words.p + 4, 0, (size_t)n_inst * sizeof(int32_t), stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "clear queues");
     const BatchArgs a = batch_args(h, P, k, counts, eps);
     int launches = 0;
@@ -696,7 +725,7 @@ te_status run_per_instance(te_handle* h, const Plan& P, int n_inst, int k, doubl
         BatchArgs ai = a;
         ai.item_base = I.item_begin;
         ai.n_items = I.n_items;
-        ai.queue = h->d_words.p + 3 + i;
+        ai.queue = h->d_words.p + 4 + i;
         if (h->profiling && i == 0 && (e = cudaEventRecord(h->ev0, stream)) != cudaSuccess)
             return h->cuda_fail(e, "event");
         if ((e = te::launch_batched(P.var, ai, std::min(I.n_items, P.grid), P.threads, P.smem, stream)) !=
@@ -731,7 +760,7 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
     cudaError_t e;
     if ((e = h->d_insts.ensure(P.insts.size(), &grew)) != cudaSuccess ||
         (e = h->d_items.ensure(P.items.size(), &grew)) != cudaSuccess ||
-        (e = h->d_words.ensure(3 + (size_t)n_inst, &grew)) != cudaSuccess ||
+        (e = h->d_words.ensure(4 + (size_t)n_inst, &grew)) != cudaSuccess ||
         (e = h->d_partial.ensure((size_t)P.n_parts, &grew)) != cudaSuccess ||
         (e = h->d_partial_abs.ensure((size_t)P.n_parts, &grew)) != cudaSuccess ||
         (n_groups > 0 && (e = h->d_te_all.ensure((size_t)n_inst, &grew)) != cudaSuccess))
@@ -756,7 +785,7 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
     const int cfg[] = {k, P.threads, P.grid, P.smem_floats, P.var.dlo, P.var.dhi, P.var.ks, P.var.qpt,
                        P.var.warp_only ? 1 : 0,
                        n_groups, S, h->profiling ? 1 : 0, n_inst, P.var.sweep ? 1 : 0, P.bd, P.bgrid,
-                       (int)P.bsmem};
+                       (int)P.bsmem, P.tgrid, (int)P.tsmem, P.n_bres};
     key = fnv(key, cfg, sizeof cfg);
     const bool replay = !h->per_instance && h->graph_exec && h->graph_key == key &&
                         h->graph_gen == h->workspace_gen;
@@ -775,7 +804,7 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
             return h->cuda_fail(e, "begin capture");
         cudaError_t ce = cudaMemsetAsync(h->d_words.p, 0, sizeof(int32_t), h->cap_stream);
         if (ce == cudaSuccess && !P.bitems.empty())
-            ce = cudaMemsetAsync(h->d_words.p + 2, 0, sizeof(int32_t), h->cap_stream);
+            ce = cudaMemsetAsync(h->d_words.p + 2, 0, 2 * sizeof(int32_t), h->cap_stream);
         int launches = 0;
         if (ce == cudaSuccess && P.var.sweep) {
             ce = launch_sweep_prepass(h, P, h->cap_stream);
@@ -783,13 +812,17 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
         }
         // an event recorded during capture becomes a graph node only with cudaEventRecordExternal
         if (ce == cudaSuccess && h->profiling) ce = cudaEventRecordWithFlags(h->ev0, h->cap_stream, cudaEventRecordExternal);
-        if (ce == cudaSuccess && !P.bitems.empty()) {
+        for (int tiled = 0; tiled < 2 && ce == cudaSuccess; ++tiled) {
+            const int n = tiled ? (int)P.bitems.size() - P.n_bres : P.n_bres;
+            if (n <= 0) continue;
             BatchArgs ab = a;
             ab.items = h->d_bitems.p;
-            ab.n_items = (int)P.bitems.size();
-            ab.queue = h->d_words.p + 2;
-            ab.smem_floats = (int)(P.bsmem / sizeof(float));
-            ce = te::launch_bundle(P.bd, P.var.ks, ab, P.bgrid, P.bsmem, h->cap_stream);
+            ab.item_base = tiled ? P.n_bres : 0;
+            ab.n_items = n;
+            ab.queue = h->d_words.p + 2 + tiled;
+            ab.smem_floats = (int)((tiled ? P.tsmem : P.bsmem) / sizeof(float));
+            ce = te::launch_bundle(P.bd, P.var.ks, tiled != 0, ab, tiled ? P.tgrid : P.bgrid,
+                                   tiled ? P.tsmem : P.bsmem, h->cap_stream);
             ++launches;
         }
         if (ce == cudaSuccess && !P.items.empty()) {

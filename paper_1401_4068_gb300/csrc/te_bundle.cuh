@@ -26,20 +26,21 @@ __device__ __forceinline__ float absmax_join(float a, const float (&c)[n]) {
     return absmax_range<0, n>(v);
 }
 
-// Stage a bundle in sorted order, in the grouped tile layout of te_device.cuh: first a tile of
-// the target part (1 + d coordinates: y_t, y_{t'-1}, ...), then one tile per member of its source
-// part (d coordinates), member m's at the float offset ng * 4 * (1 + d + m * d) (ng = groups of
-// four points); +inf past the last point (a padded reference is never inside any radius).
+// Stage sorted positions base .. base + nv - 1 of a bundle, in the grouped tile layout of
+// te_device.cuh: first a tile of the target part (1 + d coordinates: y_t, y_{t'-1}, ...), then
+// one tile per member of its source part (d coordinates), member m's at the float offset
+// cap * (1 + d + m * d) (cap: points per tile, a multiple of 4); +inf past the last point (a
+// padded reference is never inside any radius).
 template <int d, int M>
 __device__ __forceinline__ void stage_bundle(const BatchArgs& a, const InstDesc& L, const int32_t* mem, int nb,
-                                             const int32_t* __restrict__ sidx, float* sm) {
+                                             const int32_t* __restrict__ sidx, int base, int nv, int cap,
+                                             float* sm) {
     constexpr int DA = 1 + d;
-    const int N = L.N;
+    const int N = nv;
     const int nfill = (N + 3) & ~3;
-    const int ng = nfill >> 2;
     for (int p = threadIdx.x; p < nfill; p += blockDim.x) {
         if (p < N) {
-            const int i = __ldg(sidx + p);
+            const int i = __ldg(sidx + base + p);
             const int r = i / L.W;
             const int t = L.t_start + (i - r * L.W);
             const float* y = L.tgt + (size_t)r * L.T;
@@ -57,10 +58,10 @@ __device__ __forceinline__ void stage_bundle(const BatchArgs& a, const InstDesc&
         const int32_t* perm = J.perm;
         const float* src = J.src;
         const int u = J.u, R = J.R;
-        float* col = sm + ng * 4 * (DA + m * d);
+        float* col = sm + cap * (DA + m * d);
         for (int p = threadIdx.x; p < nfill; p += blockDim.x) {
             if (p < N) {
-                const int i = __ldg(sidx + p);
+                const int i = __ldg(sidx + base + p);
                 const int r = i / L.W;
                 const int t = L.t_start + (i - r * L.W);
                 int rs = r;
@@ -140,7 +141,8 @@ __device__ __forceinline__ void bknn_group(const float* __restrict__ s, const in
 template <int d, int Q, int KS, int M>
 __device__ __forceinline__ int bknn_range(const float* __restrict__ s, const int (&coff)[M], int g0, int g1,
                                           int dir, const u64 (&qa)[Q][1 + d], const u64 (&qc)[M][Q][d],
-                                          const float (&qkey)[Q], const bool (&qv)[Q], float (&t)[M][Q][KS]) {
+                                          const float (&qkey)[Q], const bool (&qv)[Q], float (&t)[M][Q][KS],
+                                          bool& done) {
     float r[Q], lb, rb;
     bundle_radii<Q, KS, M>(t, r);
     warp_window(qkey, qv, r, lb, rb);
@@ -148,8 +150,14 @@ __device__ __forceinline__ int bknn_range(const float* __restrict__ s, const int
 #pragma unroll 1
     for (int jj = g0; jj < g1; ++jj) {
         const int j = dir < 0 ? g1 - 1 - (jj - g0) : jj;
-        if (dir > 0 && group_key_lo<1 + d>(s, j) >= rb) break;
-        if (dir < 0 && group_key_hi<1 + d>(s, j) <= lb) break;
+        if (dir > 0 && group_key_lo<1 + d>(s, j) >= rb) {
+            done = true;
+            break;
+        }
+        if (dir < 0 && group_key_hi<1 + d>(s, j) <= lb) {
+            done = true;
+            break;
+        }
         bknn_group<d, Q, KS, M>(s, coff, j, qa, qc, t);
         if ((++n & 3) == 0 && dir != 0) {
             bundle_radii<Q, KS, M>(t, r);
@@ -265,9 +273,10 @@ __device__ __forceinline__ void bundle_warp_block(const BatchArgs& a, const Inst
             for (int s = 0; s < KS; ++s) t[m][q][s] = f_inf();
     const int g_own0 = wbase >> 2;
     const int g_own1 = min(ng, (min(wbase + 32 * Q, N) + 3) >> 2);
-    groups_done += bknn_range<d, Q, KS, M>(sm, coff, g_own0, g_own1, 0, qa, qc, qkey, qv, t);
-    groups_done += bknn_range<d, Q, KS, M>(sm, coff, g_own1, ng, +1, qa, qc, qkey, qv, t);
-    groups_done += bknn_range<d, Q, KS, M>(sm, coff, 0, g_own0, -1, qa, qc, qkey, qv, t);
+    bool done = false;
+    groups_done += bknn_range<d, Q, KS, M>(sm, coff, g_own0, g_own1, 0, qa, qc, qkey, qv, t, done);
+    groups_done += bknn_range<d, Q, KS, M>(sm, coff, g_own1, ng, +1, qa, qc, qkey, qv, t, done);
+    groups_done += bknn_range<d, Q, KS, M>(sm, coff, 0, g_own0, -1, qa, qc, qkey, qv, t, done);
     float e[M][Q], emax[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -345,12 +354,219 @@ __device__ __forceinline__ void bundle_warp_block(const BatchArgs& a, const Inst
     }
 }
 
-// The bundle kernel: a CTA takes a bundle (its leader's work item) from the queue, stages it,
-// and its warps take 32*Q-query blocks from a CTA-local counter. Three CTAs per SM for d <= 3
-// (a C3-sized bundle, 1200 points x 13 columns, takes 62 KB of shared memory), two above.
+// A bundle too large to stage whole: a CTA takes a block of blockDim.x * Q consecutive sorted
+// queries (one work item; `item` is its index within the bundle) and stages tiles of `cap` points
+// (a multiple of the query block, so the block lies in one tile) around it, as process_item_sweep
+// does for one estimate: the own tile first, then tiles to the right and to the left while any
+// warp's key window reaches them, then pass 2 over the tiles of the CTA's key window. Windows use
+// the largest radius over the members; the partial sums are per CTA block and member.
 template <int d, int Q, int KS, int M>
+__device__ __forceinline__ void bundle_item_tiled(const BatchArgs& a, const InstDesc& L, const int32_t* mem, int nb,
+                                                  int q0, int item, float* sm, double* sred, float* sbnd) {
+    constexpr int DA = 1 + d;
+    constexpr int D = 1 + 2 * d;
+    const int N = L.N;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int32_t* sidx = a.sorted_idx + L.sort_off;
+    const float* skey = a.sorted_key + L.sort_off;
+    const int block = blockDim.x * Q;
+    const int cap = ((a.smem_floats / (DA + M * d)) / block) * block;  // points per tile
+    const int ntile = (N + cap - 1) / cap;
+    const int ctile = q0 / cap;
+    int coff[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) coff[m] = cap * (DA + min(m, nb - 1) * d);
+
+    // queries: warp-contiguous runs of the sorted order, gathered from the series (Eq. 6 / 7)
+    const int wbase = q0 + warp * 32 * Q;
+    u64 qa[Q][DA];
+    u64 qc[M][Q][d];
+    float qkey[Q];
+    int qidx[Q];
+    bool qv[Q];
+    int nvalid = 0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int pos = wbase + q * 32 + lane;
+        qv[q] = pos < N;
+        qidx[q] = qv[q] ? __ldg(sidx + pos) : 0;
+        const int r = qidx[q] / L.W;
+        const int tt = L.t_start + (qidx[q] - r * L.W);
+        const float* y = L.tgt + (size_t)r * L.T;
+        qa[q][0] = dup2(qv[q] ? __ldg(y + tt) : 0.0f);
+#pragma unroll
+        for (int c = 0; c < d; ++c) qa[q][1 + c] = dup2(qv[q] ? __ldg(y + tt - 1 - c * L.tau) : 0.0f);
+        qkey[q] = qv[q] ? __ldg(y + tt - 1) : 0.0f;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const InstDesc& J = a.insts[mem[min(m, nb - 1)]];
+            int rs = r;
+            if (J.perm && qv[q]) {
+                rs = __ldg(J.perm + r);
+                if ((unsigned)rs >= (unsigned)J.R) {
+                    atomicOr(a.flags, kFlagBadPerm);
+                    rs = 0;
+                }
+            }
+            const float* x = J.src + (size_t)rs * L.T;
+#pragma unroll
+            for (int c = 0; c < d; ++c) qc[m][q][c] = dup2(qv[q] ? __ldg(x + tt - J.u - c * L.tau) : 0.0f);
+        }
+        nvalid += __popc(__ballot_sync(0xffffffffu, qv[q]));
+        if (!qv[q]) qidx[q] = -1;
+    }
+    const bool warp_active = wbase < N;
+    unsigned long long groups_done = 0;
+
+    int staged = -1;
+    auto stage = [&](int ti) {
+        if (staged == ti) return;
+        const int base = ti * cap;
+        __syncthreads();
+        stage_bundle<d, M>(a, L, mem, nb, sidx, base, min(cap, N - base), cap, sm);
+        __syncthreads();
+        staged = ti;
+    };
+    auto ngroups = [&](int ti) { return (min(cap, N - ti * cap) + 3) >> 2; };
+
+    // ---- pass 1: own block, then right, then left
+    float t[M][Q][KS];
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int s = 0; s < KS; ++s) t[m][q][s] = f_inf();
+    bool rdone = false, ldone = false;
+    stage(ctile);
+    if (warp_active) {
+        const int g_own0 = (wbase - ctile * cap) >> 2;
+        const int g_own1 = min(ngroups(ctile), (min(wbase + 32 * Q, N) - ctile * cap + 3) >> 2);
+        groups_done += bknn_range<d, Q, KS, M>(sm, coff, g_own0, g_own1, 0, qa, qc, qkey, qv, t, rdone);
+        rdone = false;
+        groups_done += bknn_range<d, Q, KS, M>(sm, coff, g_own1, ngroups(ctile), +1, qa, qc, qkey, qv, t, rdone);
+        groups_done += bknn_range<d, Q, KS, M>(sm, coff, 0, g_own0, -1, qa, qc, qkey, qv, t, ldone);
+    }
+    for (int ti = ctile + 1; ti < ntile; ++ti) {  // right tiles
+        float r[Q], lb, rb;
+        bundle_radii<Q, KS, M>(t, r);
+        warp_window(qkey, qv, r, lb, rb);
+        float blb = f_inf(), brb = (warp_active && !rdone) ? rb : -f_inf();
+        block_minmax(blb, brb, sbnd);
+        if (!(__ldg(skey + ti * cap) < brb)) break;
+        stage(ti);
+        if (warp_active && !rdone)
+            groups_done += bknn_range<d, Q, KS, M>(sm, coff, 0, ngroups(ti), +1, qa, qc, qkey, qv, t, rdone);
+    }
+    for (int ti = ctile - 1; ti >= 0; --ti) {  // left tiles
+        float r[Q], lb, rb;
+        bundle_radii<Q, KS, M>(t, r);
+        warp_window(qkey, qv, r, lb, rb);
+        float blb = (warp_active && !ldone) ? lb : f_inf(), brb = -f_inf();
+        block_minmax(blb, brb, sbnd);
+        if (!(__ldg(skey + (ti + 1) * cap - 1) > blb)) break;
+        stage(ti);
+        if (warp_active && !ldone)
+            groups_done += bknn_range<d, Q, KS, M>(sm, coff, 0, ngroups(ti), -1, qa, qc, qkey, qv, t, ldone);
+    }
+    float e[M][Q], emax[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        emax[q] = 0.0f;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            e[m][q] = topk_select(t[m][q], a.k);
+            emax[q] = fmaxf(emax[q], e[m][q]);
+        }
+    }
+
+    // ---- pass 2: the tiles of the CTA's key window (largest eps over the members)
+    float cz[M][Q], cyz[M][Q], cxz[M][Q];
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) cz[m][q] = cyz[m][q] = cxz[m][q] = 0.0f;
+    float lb, rb;
+    warp_window(qkey, qv, emax, lb, rb);
+    float blb = warp_active ? lb : f_inf(), brb = warp_active ? rb : -f_inf();
+    block_minmax(blb, brb, sbnd);
+    const int plo = first_greater(skey, N, blb);
+    const int phi = first_not_less(skey, N, brb);
+    if (plo < phi) {
+        for (int ti = plo / cap; ti <= (phi - 1) / cap; ++ti) {
+            stage(ti);
+            if (warp_active)
+                groups_done += bcount_range<d, Q, M>(sm, coff, 0, ngroups(ti), lb, rb, qa, qc, e, cz, cyz, cxz);
+        }
+    }
+
+    // ---- per member: digamma terms of Eq. 9, FP64 partial per CTA block
+#pragma unroll 1
+    for (int m = 0; m < nb; ++m) {
+        const InstDesc& J = a.insts[mem[m]];
+        const int64_t pt_off = J.pt_off;
+        FF acc{0.0f, 0.0f};
+        float acc_abs = 0.0f;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            float em = e[0][q], cm = cz[0][q], cym = cyz[0][q], cxm = cxz[0][q];
+#pragma unroll
+            for (int mm = 1; mm < M; ++mm)
+                if (mm == m) {
+                    em = e[mm][q];
+                    cm = cz[mm][q];
+                    cym = cyz[mm][q];
+                    cxm = cxz[mm][q];
+                }
+            if (qv[q]) {
+                const int i = qidx[q];
+                const int self = em > 0.0f ? 1 : 0;
+                const int nz = (int)cm - self, nyz = (int)cym - self, nxz = (int)cxm - self;
+                if (a.counts_out) {
+                    int32_t* co = a.counts_out + 3 * pt_off;
+                    co[i] = nz;
+                    co[N + i] = nyz;
+                    co[2 * N + i] = nxz;
+                }
+                if (a.eps_out) a.eps_out[pt_off + i] = em;
+                const float2 p1 = __ldg(a.psi + nz + 1);
+                const float2 p2 = __ldg(a.psi + nyz + 1);
+                const float2 p3 = __ldg(a.psi + nxz + 1);
+                acc = ff_add(acc, p1.x, p1.y);
+                acc = ff_add(acc, -p2.x, -p2.y);
+                acc = ff_add(acc, -p3.x, -p3.y);
+                acc_abs += fabsf(p1.x) + fabsf(p2.x) + fabsf(p3.x);
+            }
+        }
+        double v = (double)acc.hi + (double)acc.lo;
+        double w = (double)acc_abs;
+        __syncthreads();  // sred of the previous member is read
+        block_sum2(v, w, sred);
+        if (threadIdx.x == 0) {
+            a.partial[J.part_begin + item] = v;
+            a.partial_abs[J.part_begin + item] = w;
+        }
+    }
+    if (a.exec && warp_active && lane == 0) {
+        const unsigned long long g4 = groups_done * 4ull * (unsigned long long)nvalid;
+        const unsigned long long alg = g4 * (unsigned long long)nb * 2ull * D;
+        const unsigned long long run = g4 * (2ull * DA + (unsigned long long)M * 2ull * d);
+        atomicAdd(a.exec, g4 * (unsigned long long)nb);
+        atomicAdd(a.exec + 1, alg);
+        atomicAdd(a.exec + 2, alg > run ? alg - run : 0ull);
+    }
+}
+
+// The bundle kernel: a CTA takes a bundle (its leader's work item) from the queue, stages it,
+// and its warps take 32*Q-query blocks from a CTA-local counter; TILED: bundles too large to stage
+// whole, one CTA query block per work item (a separate instantiation, so that the resident path
+// keeps the registers it needs without the tiled path's). Three CTAs per SM for d <= 3
+// (a C3-sized bundle, 1200 points x 13 columns, takes 62 KB of shared memory), two above.
+template <int d, int Q, int KS, int M, bool TILED>
 __global__ void __launch_bounds__(kBundleThreads, d <= 3 ? 3 : 2) bundle_kernel(const BatchArgs a) {
     extern __shared__ __align__(16) float sm[];
+    __shared__ double sred[64];
+    __shared__ float sbnd[64];
     __shared__ int s_item;
     __shared__ int s_wblock;
     for (;;) {
@@ -363,7 +579,14 @@ __global__ void __launch_bounds__(kBundleThreads, d <= 3 ? 3 : 2) bundle_kernel(
         const InstDesc L = a.insts[w.inst];
         const int32_t* mem = a.members + L.bundle_off;
         const int nb = L.bundle_n;
-        stage_bundle<d, M>(a, L, mem, nb, a.sorted_idx + L.sort_off, sm);
+        if constexpr (TILED) {  // too large to stage whole: CTA tiles around a block of queries
+            bundle_item_tiled<d, Q, KS, M>(a, L, mem, nb, w.q0, w.q0 / (int)(blockDim.x * Q), sm, sred, sbnd);
+            continue;
+        } else {
+            (void)sred;
+            (void)sbnd;
+        }
+        stage_bundle<d, M>(a, L, mem, nb, a.sorted_idx + L.sort_off, 0, L.N, (L.N + 3) & ~3, sm);
         if (threadIdx.x == 0) s_wblock = w.q0;
         __syncthreads();
         const int wb1 = min((L.N + 32 * Q - 1) / (32 * Q), w.q0 + L.wb_chunk);

@@ -116,8 +116,8 @@ cudaError_t launch_batched(const BatchedVariant& v, const BatchArgs& a, int grid
 constexpr int kBundleMax = 3;       // members per bundle
 constexpr int kBundleQ = 1;         // queries per thread
 constexpr int kBundleThreads = 256;
-const void* bundle_kernel_ptr(int d, int ks);
-cudaError_t launch_bundle(int d, int ks, const BatchArgs& a, int grid, size_t smem, cudaStream_t s);
+const void* bundle_kernel_ptr(int d, int ks, bool tiled);
+cudaError_t launch_bundle(int d, int ks, bool tiled, const BatchArgs& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_finalize_te(const InstDesc* insts, int n_inst, const double* partial,
                                const double* partial_abs, double psi_k, double err_coef,
                                double* te, double* err, cudaStream_t s);

@@ -118,3 +118,51 @@ def test_bad_permutation_entry_in_a_bundle_is_flagged(te_handle):
     assert te.te_last_alu_ops(te_handle)[1] == 1
     with pytest.raises(te.TEError, match="TE_EINVAL"):
         te.te_sync_status(te_handle)
+
+
+def test_tiled_bundles_match_unshared_and_oracle(te_handle):
+    """Estimates too large for shared memory on their own (7500 points x 7 = 210 KB; a bundle of
+    three 390 KB) run in tiled bundles; radii and counts equal the unshared search bit for bit and
+    the oracle on sampled estimates."""
+    w = I.config(3, n_t=2, S=4, R=2500)  # 5 estimates per start: bundles of 3 + 2
+    ds = te.to_device(w.series)
+    off, b0, _, _, _ = _estimate(te_handle, ds, w.instances, w.k, False)
+    on, b1, ops1, alg1, swept = _estimate(te_handle, ds, w.instances, w.k, True)
+    assert swept and b0 == 0 and b1 == 4 and ops1 < alg1
+    assert torch.equal(off["counts"], on["counts"]) and torch.equal(off["eps"], on["eps"])
+    assert torch.max(torch.abs(off["te"] - on["te"])).item() <= 1e-12
+    idx = [0, 3, 7]
+    o_te, o_counts, o_eps = oracle.te_batch(w.series, [w.instances[i] for i in idx], w.k, want_counts=True)
+    N = w.n_points(w.instances[0])
+    eps = on["eps"].cpu().numpy().reshape(-1, N)
+    counts = on["counts"].cpu().numpy().reshape(-1, 3 * N)
+    for j, i in enumerate(idx):
+        np.testing.assert_array_equal(eps[i], o_eps[j * N:(j + 1) * N])
+        np.testing.assert_array_equal(counts[i], o_counts[3 * j * N:3 * (j + 1) * N])
+    assert np.max(np.abs(on["te"].cpu().numpy()[idx] - o_te)) <= TOL
+
+
+def test_delay_scan_with_tiled_bundles(te_handle):
+    """A delay scan whose windows are too large to stay resident (Lorenz, 150 repetitions x 250
+    samples = 37,500 points, d = 4) shares the target part across delays and surrogates in tiled
+    bundles; the scan equals the unshared one, and the original at u = 45 matches the oracle on
+    sampled query points. AR(1) windows (15,000 points, d = 1) stay resident and unshared."""
+    w = I.lorenz_analysis(S=2)
+    ds = te.to_device(w.series)
+    starts = w.t_starts[0][1:2]
+    te.te_set_sharing(te_handle, False)
+    try:
+        off = te.te_delay_scan(te_handle, ds[0], starts, w.window, 44, 46, w.S, w.k)
+        torch.cuda.synchronize()
+    finally:
+        te.te_set_sharing(te_handle, True)
+    on = te.te_delay_scan(te_handle, ds[0], starts, w.window, 44, 46, w.S, w.k)
+    torch.cuda.synchronize()
+    assert te.te_last_alu_ops(te_handle)[1] == 3  # 3 delays x 3 estimates = 9
+    assert torch.max(torch.abs(off["te"] - on["te"])).item() <= 1e-12
+    assert torch.equal(off["p"], on["p"]) and torch.equal(off["u_best"], on["u_best"])
+    wa = I.ar1_analysis("unidirectional", S=4, R=50, window=300, n_windows=1)
+    dsa = te.to_device(wa.series)
+    te.te_delay_scan(te_handle, dsa[0], wa.t_starts[0], wa.window, 8, 10, wa.S, wa.k)
+    torch.cuda.synchronize()
+    assert te.te_last_alu_ops(te_handle)[1] == 0
