@@ -106,6 +106,7 @@ struct Plan {
     std::vector<WorkItem> items;  // cost order, items of an instance contiguous
     std::vector<te::SortGroup> groups;  // sweep mode: one sorted order per (series, start, window)
     int64_t sorted_total = 0;
+    int64_t strip_total = 0;        // strip table entries (S + 1 per striped group)
     int nmax = 0;
     int n_parts = 0;                // partial sums (per CTA query block or per warp block)
     uint64_t exhaustive_pairs = 0;  // pair evaluations of the exhaustive search (both passes)
@@ -176,8 +177,9 @@ struct te_handle {
     DevBuf<double> d_partial, d_partial_abs, d_te_all, d_surr_ws, d_p_ws;
     DevBuf<float2> d_psi;
     DevBuf<te::SortGroup> d_groups;
-    DevBuf<int32_t> d_sidx, d_sidx_tmp;
-    DevBuf<float> d_skey, d_skey_tmp;
+    DevBuf<int32_t> d_sidx, d_sia, d_sib, d_strip_pos;
+    DevBuf<float> d_skey, d_strip_k2;
+    DevBuf<unsigned long long> d_sk64a, d_sk64b;
     DevBuf<unsigned long long> d_exec;
     DevBuf<WorkItem> d_bitems;
     DevBuf<int32_t> d_members;
@@ -335,6 +337,7 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
                      int n_inst, int k, Plan* P) {
     P->insts.resize(n_inst);
     int dlo = 99, dhi = 0, nmax = 0, dmaxN = 0;
+    int dmaxN_strips = 0;  // dmaxN with the padding of the strips a group of this size may get
     int64_t off = 0;
     for (int i = 0; i < n_inst; ++i) {
         const te_instance& in = inst[i];
@@ -368,6 +371,8 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
         dhi = std::max(dhi, S.d);
         nmax = std::max(nmax, (int)N);
         dmaxN = std::max(dmaxN, (int)(((N + 3) & ~3) * (1 + 2 * S.d)));
+        const int ns = std::min<int>(te::kMaxStrips, (int)(N / te::kStripPoints));
+        dmaxN_strips = std::max(dmaxN_strips, (int)(((N + 3 * (ns >= 4 ? ns : 0) + 3) & ~3) * (1 + 2 * S.d)));
     }
     P->n_points = off;
     if (dlo != dhi && dhi > kMaxMixedD)
@@ -400,7 +405,7 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
         // every instance resident in shared memory (up to kResidentMaxBytes) when it fits there,
         // which lets warps balance the work; otherwise tiles of whole CTA query blocks
         if (!h->per_instance && (int64_t)dmaxN * (int64_t)sizeof(float) <= kResidentMaxBytes) {
-            P->smem_floats = std::max(P->smem_floats, dmaxN);
+            P->smem_floats = std::max(P->smem_floats, std::min(dmaxN_strips, (int)(kResidentMaxBytes / 4)));
         } else {
             int need = P->smem_floats;
             for (const auto& I : P->insts) {
@@ -516,15 +521,83 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
         P->n_bres = (int)P->bitems.size();
         P->bitems.insert(P->bitems.end(), titems.begin(), titems.end());
     }
+    // warp mode of every unshared estimate: staged whole when it fits shared memory
+    for (int i = 0; i < n_inst; ++i) {
+        InstDesc& I = P->insts[i];
+        I.strips = 1;
+        I.npad = I.N;
+        I.strip_off = 0;
+        if (bundled[i]) continue;
+        const bool fits = (int64_t)((I.N + 3) & ~3) * (1 + 2 * I.d) <= P->smem_floats;
+        I.warp_mode = (sweep && fits && !h->per_instance) ? 1 : 0;
+    }
+    // sort groups: one per (target series, repetitions, window start, window); a group whose every
+    // estimate is staged whole and unshared and that agrees on the second key is cut into strips
+    // (about kStripPoints points each, at least 4) when the padded positions still fit
+    if (sweep) {
+        std::map<std::tuple<const float*, int, int, int, int>, std::vector<int>> gmem;
+        std::vector<std::tuple<const float*, int, int, int, int>> gorder;
+        for (int i = 0; i < n_inst; ++i) {
+            const InstDesc& I = P->insts[i];
+            auto key = std::make_tuple(I.tgt, I.T, I.R, I.t_start, I.W);
+            auto f = gmem.find(key);
+            if (f == gmem.end()) {
+                gorder.push_back(key);
+                f = gmem.emplace(key, std::vector<int>()).first;
+            }
+            f->second.push_back(i);
+        }
+        int64_t strip_total = 0;
+        for (const auto& key : gorder) {
+            const std::vector<int>& v = gmem[key];
+            const InstDesc& I0 = P->insts[v[0]];
+            const int N = I0.N;
+            const int k2lag = I0.d >= 2 ? 1 + I0.tau : 0;
+            int S = std::min(te::kMaxStrips, N / te::kStripPoints);
+            int npad = N;
+            if (S >= 4) {
+                npad = 0;
+                for (int st = 0; st < S; ++st) {
+                    const int64_t a = ((int64_t)st * N + S - 1) / S, b = ((int64_t)(st + 1) * N + S - 1) / S;
+                    npad += (int)((b - a + 3) & ~3);
+                }
+                for (int i : v) {
+                    const InstDesc& I = P->insts[i];
+                    const int lag = I.d >= 2 ? 1 + I.tau : 0;
+                    if (bundled[i] || I.warp_mode != 1 || lag != k2lag ||
+                        (int64_t)((npad + 3) & ~3) * (1 + 2 * I.d) > P->smem_floats)
+                        S = 1;
+                }
+            }
+            if (S < 4) {
+                S = 1;
+                npad = N;
+            }
+            te::SortGroup G{I0.tgt, I0.R, I0.T, I0.W, I0.t_start, N, S, npad, k2lag, P->sorted_total,
+                            S > 1 ? strip_total : 0};
+            P->groups.push_back(G);
+            for (int i : v) {
+                InstDesc& I = P->insts[i];
+                I.sort_off = P->sorted_total;
+                I.strips = S;
+                I.npad = npad;
+                I.strip_off = G.strip_off;
+            }
+            P->sorted_total += npad;
+            if (S > 1) strip_total += S + 1;
+        }
+        P->strip_total = strip_total;
+    }
+    // work items of the unshared estimates (cost order, an estimate's items contiguous) and their
+    // partial-sum ranges: a staged-whole estimate is cut into items of warp blocks (32 * qpt
+    // sorted positions), any other into CTA query blocks
     for (int i : order) {
         if (bundled[i]) continue;
         InstDesc& I = P->insts[i];
-        const bool fits = (int64_t)((I.N + 3) & ~3) * (1 + 2 * I.d) <= P->smem_floats;
-        I.warp_mode = (sweep && fits && !h->per_instance) ? 1 : 0;
         I.item_begin = (int)P->items.size();
         I.part_begin = n_parts;
         if (I.warp_mode) {
-            const int nwb = (I.N + 32 * qpt - 1) / (32 * qpt);
+            const int nwb = (I.npad + 32 * qpt - 1) / (32 * qpt);
             const int split = std::max(1, std::min(nwb, (want_items + n_inst - 1) / n_inst));
             I.wb_chunk = (nwb + split - 1) / split;
             I.n_items = (nwb + I.wb_chunk - 1) / I.wb_chunk;
@@ -539,20 +612,6 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
         max_parts = std::max(max_parts, I.n_parts);
     }
     P->n_parts = n_parts;
-    if (sweep) {
-        std::map<std::tuple<const float*, int, int, int, int>, int64_t> gidx;
-        for (auto& I : P->insts) {
-            auto key = std::make_tuple(I.tgt, I.T, I.R, I.t_start, I.W);
-            auto f = gidx.find(key);
-            if (f == gidx.end()) {
-                te::SortGroup G{I.tgt, I.R, I.T, I.W, I.t_start, I.N, 0, P->sorted_total};
-                P->groups.push_back(G);
-                f = gidx.emplace(key, P->sorted_total).first;
-                P->sorted_total += I.N;
-            }
-            I.sort_off = f->second;
-        }
-    }
     // every unshared estimate staged whole with one d <= 2: the warp-mode sweep kernel (1024-thread
     // CTAs unless a shape was set or tuned for this signature)
     bool all_warp = !P->items.empty();
@@ -663,9 +722,12 @@ te_status prepare_sweep(te_handle* h, const Plan& P, bool* grew) {
         (e = h->d_bitems.ensure(P.bitems.size(), grew)) != cudaSuccess ||
         (e = h->d_members.ensure(P.members.size(), grew)) != cudaSuccess)
         return h->fail(TE_ENOMEM, "sweep workspace: %s", cudaGetErrorString(e));
-    if (te::sort_needs_scratch(P.nmax) &&
-        ((e = h->d_sidx_tmp.ensure((size_t)P.sorted_total, grew)) != cudaSuccess ||
-         (e = h->d_skey_tmp.ensure((size_t)P.sorted_total, grew)) != cudaSuccess))
+    if ((e = h->d_sia.ensure((size_t)P.sorted_total, grew)) != cudaSuccess ||
+        (e = h->d_sib.ensure((size_t)P.sorted_total, grew)) != cudaSuccess ||
+        (e = h->d_sk64a.ensure((size_t)P.sorted_total, grew)) != cudaSuccess ||
+        (e = h->d_sk64b.ensure((size_t)P.sorted_total, grew)) != cudaSuccess ||
+        (e = h->d_strip_pos.ensure((size_t)std::max<int64_t>(1, P.strip_total), grew)) != cudaSuccess ||
+        (e = h->d_strip_k2.ensure((size_t)std::max<int64_t>(2, 2 * P.strip_total), grew)) != cudaSuccess)
         return h->fail(TE_ENOMEM, "sort scratch: %s", cudaGetErrorString(e));
     if ((e = te::prepare_sort_kernel(P.nmax)) != cudaSuccess) return h->cuda_fail(e, "sort kernel attribute");
     return TE_OK;
@@ -676,8 +738,8 @@ cudaError_t launch_sweep_prepass(te_handle* h, const Plan& P, cudaStream_t s) {
     if (!P.var.sweep) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(h->d_exec.p, 0, 3 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    return te::launch_sort_groups(h->d_groups.p, (int)P.groups.size(), P.nmax, h->d_sidx.p, h->d_skey.p,
-                                  h->d_sidx_tmp.p, h->d_skey_tmp.p, s);
+    return te::launch_sort_groups(h->d_groups.p, (int)P.groups.size(), h->d_sidx.p, h->d_skey.p, h->d_sk64a.p,
+                                  h->d_sia.p, h->d_sk64b.p, h->d_sib.p, h->d_strip_pos.p, h->d_strip_k2.p, s);
 }
 
 BatchArgs batch_args(te_handle* h, const Plan& P, int k, int32_t* counts, float* eps) {
@@ -700,6 +762,8 @@ BatchArgs batch_args(te_handle* h, const Plan& P, int k, int32_t* counts, float*
         a.sorted_key = h->d_skey.p;
         a.exec = h->d_exec.p;
         a.members = h->d_members.p;
+        a.strip_pos = h->d_strip_pos.p;
+        a.strip_k2 = h->d_strip_k2.p;
     }
     return a;
 }
@@ -923,8 +987,12 @@ TE_EXPORT void te_destroy(te_handle* h) {
     h->d_groups.release();
     h->d_sidx.release();
     h->d_skey.release();
-    h->d_sidx_tmp.release();
-    h->d_skey_tmp.release();
+    h->d_sia.release();
+    h->d_sib.release();
+    h->d_sk64a.release();
+    h->d_sk64b.release();
+    h->d_strip_pos.release();
+    h->d_strip_k2.release();
     h->d_exec.release();
     h->d_bitems.release();
     h->d_members.release();

@@ -26,16 +26,32 @@ struct InstDesc {
     int32_t wb_chunk;      // warp mode: warp blocks per work item (an item's q0 is its first block)
     int32_t bundle_n;      // bundle leader: members that share its target part (0: not a leader)
     int32_t bundle_off;    // bundle leader: its members' instance indices start at members[bundle_off]
+    int32_t strips;        // sweep: strips of its sort group (1: one key order, see SortGroup)
+    int32_t npad;          // sweep: sorted positions of its group (N plus strip padding)
+    int64_t strip_off;     // strips > 1: its group's strip table at strip_pos / strip_k2
 };
 
 // Points of one (series, window start, window) group: the estimates of a group (original and
 // surrogates) share the target coordinates, so they share one order of the points sorted by the
-// target coordinate y_{t'-1} (coordinate 1 of the joint space).
+// target coordinate y_{t'-1} (coordinate 1 of the joint space). With S > 1 strips the points are
+// first cut by a second target coordinate y_{t'-k2lag} into S strips of equal count, each sorted
+// by y_{t'-1} and padded to a multiple of four positions (index -1, key +inf), so that a 4-point
+// group never spans two strips; strip s holds positions strip_pos[s] .. strip_pos[s+1]-1 and its
+// second-key values lie in [strip_k2[2s], strip_k2[2s+1]]. The second key is y_{t'-1-tau}
+// (coordinate 2, in y-) for d >= 2 and y_t (coordinate 0, not in y-) for d = 1.
 struct SortGroup {
     const float* tgt;
-    int32_t R, T, W, t_start, N, pad;
-    int64_t off;           // offset of the group's sorted index / key arrays
+    int32_t R, T, W, t_start, N;
+    int32_t S;             // strips (1: one key order)
+    int32_t npad;          // sorted positions (N when S == 1)
+    int32_t k2lag;         // S > 1: the second key is y_{t' - k2lag}
+    int64_t off;           // offset of the group's sorted index / key arrays (npad entries)
+    int64_t strip_off;     // S > 1: strip_pos[strip_off .. strip_off + S], strip_k2[2 strip_off ..
+                           // 2 strip_off + 2 S - 1]
 };
+
+constexpr int kStripPoints = 1024;  // target points per strip
+constexpr int kMaxStrips = 64;
 
 // Largest point count the sweep mode sorts (one CTA per group; runs in shared memory, merges
 // through global memory above 8192 points).
@@ -74,6 +90,8 @@ struct BatchArgs {
     unsigned long long* exec;   // sweep mode: [0] evaluated (query, reference) pairs, [1] their
                                 // 2 D FP32 ops, [2] ops not executed thanks to target-part sharing
     const int32_t* members;     // bundle kernel: member instance indices (leader first)
+    const int32_t* strip_pos;   // sweep with strips: per group S + 1 sorted positions
+    const float* strip_k2;      // sweep with strips: per group S (lowest, highest) y_t
 };
 
 // ---- launchers (te_unit.cu) ----
@@ -93,9 +111,11 @@ struct BatchedVariant {
     bool sweep;      // sorted-sweep search instead of the exhaustive one
     bool warp_only;  // sweep_warp_kernel: every estimate staged whole, d = dlo = dhi <= 2, ks = 5
 };
-cudaError_t launch_sort_groups(const SortGroup* groups, int n_groups, int nmax, int32_t* idx, float* key,
-                               int32_t* tmp_idx, float* tmp_key, cudaStream_t s);
-bool sort_needs_scratch(int nmax);  // tmp_idx / tmp_key (sorted_total entries) are used
+// Sort pre-pass: sorted index / key arrays (npad per group) and the strip tables; scratch: two
+// (64-bit key, index) buffers of N entries per group at the group's offset.
+cudaError_t launch_sort_groups(const SortGroup* groups, int n_groups, int32_t* idx, float* key,
+                               unsigned long long* k64a, int32_t* ia, unsigned long long* k64b, int32_t* ib,
+                               int32_t* strip_pos, float* strip_k2, cudaStream_t s);
 cudaError_t prepare_sort_kernel(int nmax);
 const void* batched_kernel_ptr(const BatchedVariant& v);
 const void* batched_ptr_d1(int ks, int q, bool sweep);

@@ -56,8 +56,9 @@ __device__ __forceinline__ void stage_tile_sorted(const InstDesc& I, const int32
     const int nfill = (nv + 3) & ~3;
     for (int p = threadIdx.x; p < nfill; p += blockDim.x) {
         float v[D];
-        if (p < nv) {
-            gather_point<d>(I, __ldg(sidx + base + p), v, flags);
+        const int i = p < nv ? __ldg(sidx + base + p) : -1;  // -1: strip padding
+        if (i >= 0) {
+            gather_point<d>(I, i, v, flags);
         } else {
 #pragma unroll
             for (int c = 0; c < D; ++c) v[c] = f_inf();
@@ -440,6 +441,193 @@ __device__ __forceinline__ void sweep_warp_block(const BatchArgs& a, const InstD
     }
 }
 
+// first group g in [g0, g1) of a staged tile with group_key_hi(g) > x (keys ascending in range)
+template <int D>
+__device__ __forceinline__ int smem_first_group_above(const float* __restrict__ s, int g0, int g1, float x) {
+    int lo = g0, hi = g1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (group_key_hi<D>(s, mid) > x) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+// sweep_warp_block for a group cut into strips (SortGroup). Two target coordinates bound the
+// distances: key1 = y_{t'-1} (coordinate 1) and key2 (coordinate K2 = 2, y_{t'-1-tau}, for d >= 2;
+// K2 = 0, y_t, for d = 1). fl(|Δkey1|) bounds from below the joint distance and b = max over y-
+// (hence max(a, b) and max(b, x)); fl(|Δkey2|) bounds the joint distance, and for d >= 2 also b.
+// A reference is skipped when one of them is >= r for every query of the warp, decided per strip
+// from its key2 range and inside a strip from its key1 order, bounds rounded outward. Pass 1: the
+// warp's own positions, its own strip(s) outward from them, then the other strips nearest first
+// in key2, each entered at the warp's middle key1 and swept both ways. Pass 2: the key1 window of
+// every strip (for d >= 2 only the strips whose key2 range meets the key2 window). Strip padding
+// (index -1, +inf coordinates) is neither a query nor ever inside a radius.
+template <int d, int Q, int KS>
+__device__ __forceinline__ void sweep_warp_block_strips(const BatchArgs& a, const InstDesc& I, const float* sm,
+                                                        int wb, int part) {
+    constexpr int D = 1 + 2 * d;
+    constexpr int K2 = d >= 2 ? 2 : 0;  // coordinate of the second key
+    const int N = I.N;
+    const int npos = I.npad;
+    const int S = I.strips;
+    const int lane = threadIdx.x & 31;
+    const int32_t* sidx = a.sorted_idx + I.sort_off;
+    const int32_t* spos = a.strip_pos + I.strip_off;
+    const float* sk2 = a.strip_k2 + 2 * I.strip_off;
+    const int wbase = wb * 32 * Q;
+    u64 qq[Q][D];
+    float qkey[Q], qk2[Q];
+    int qidx[Q];
+    bool qv[Q];
+    int nvalid = 0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int pos = wbase + q * 32 + lane;
+        qidx[q] = pos < npos ? __ldg(sidx + pos) : -1;
+        qv[q] = qidx[q] >= 0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) qq[q][c] = dup2(qv[q] ? sm[tile_index<D>(c, pos)] : 0.0f);
+        qkey[q] = qv[q] ? sm[tile_index<D>(1, pos)] : 0.0f;
+        qk2[q] = qv[q] ? sm[tile_index<D>(K2, pos)] : 0.0f;
+        nvalid += __popc(__ballot_sync(0xffffffffu, qv[q]));
+    }
+    unsigned long long groups_done = 0;
+    if (nvalid == 0) {  // a warp block of strip padding only
+        if (lane == 0) {
+            a.partial[part] = 0.0;
+            a.partial_abs[part] = 0.0;
+        }
+        return;
+    }
+    // median-ish entry key: the middle valid query key of the warp
+    float kmin = f_inf(), kmax = -f_inf();
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+        if (qv[q]) {
+            kmin = fminf(kmin, qkey[q]);
+            kmax = fmaxf(kmax, qkey[q]);
+        }
+    kmin = warp_min(kmin);
+    kmax = warp_max(kmax);
+    const float kmid = 0.5f * kmin + 0.5f * kmax;
+    // the strips holding the warp's positions
+    int s_lo = 0;
+    while (s_lo + 1 < S && __ldg(spos + s_lo + 1) <= wbase) ++s_lo;
+    int s_hi = s_lo;
+    const int wend = min(wbase + 32 * Q, npos);
+    while (s_hi + 1 < S && __ldg(spos + s_hi + 1) < wend) ++s_hi;
+    const int g_own0 = wbase >> 2, g_own1 = (wend + 3) >> 2;
+
+    // ---- pass 1
+    float t[Q][KS];
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int m = 0; m < KS; ++m) t[q][m] = f_inf();
+    bool done = false;
+    groups_done += knn_range<D, Q, KS>(sm, g_own0, g_own1, 0, qq, qkey, qv, t, done);
+    for (int s = s_lo; s <= s_hi; ++s) {  // own strip(s), outward from the own positions
+        const int gs = __ldg(spos + s) >> 2, ge = __ldg(spos + s + 1) >> 2;
+        done = false;
+        groups_done += knn_range<D, Q, KS>(sm, max(gs, g_own1), ge, +1, qq, qkey, qv, t, done);
+        done = false;
+        groups_done += knn_range<D, Q, KS>(sm, gs, min(ge, g_own0), -1, qq, qkey, qv, t, done);
+    }
+    // other strips, nearest first in key2, while their key2 range meets the window
+    bool up = s_hi + 1 < S, down = s_lo > 0;
+    for (int step = 1; up || down; ++step) {
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const int s = side == 0 ? s_hi + step : s_lo - step;
+            if (side == 0 ? (!up || s >= S) : (!down || s < 0)) {
+                if (side == 0) up = false;
+                else down = false;
+                continue;
+            }
+            float r[Q], lb2, rb2;
+            current_radii(t, r);
+            warp_window(qk2, qv, r, lb2, rb2);
+            if (side == 0 && !(__ldg(sk2 + 2 * s) < rb2)) {
+                up = false;
+                continue;
+            }
+            if (side == 1 && !(__ldg(sk2 + 2 * s + 1) > lb2)) {
+                down = false;
+                continue;
+            }
+            const int gs = __ldg(spos + s) >> 2, ge = __ldg(spos + s + 1) >> 2;
+            const int gm = smem_first_group_above<D>(sm, gs, ge, kmid);
+            done = false;
+            groups_done += knn_range<D, Q, KS>(sm, gm, ge, +1, qq, qkey, qv, t, done);
+            done = false;
+            groups_done += knn_range<D, Q, KS>(sm, gs, gm, -1, qq, qkey, qv, t, done);
+        }
+    }
+    float e[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) e[q] = topk_select(t[q], a.k);
+
+    // ---- pass 2: the key1 window of every strip (d >= 2: whose key2 range meets the window; the
+    // counts of n_z and n_xz do not involve y_t, so for d = 1 no strip is skipped)
+    float cz[Q], cyz[Q], cxz[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) cz[q] = cyz[q] = cxz[q] = 0.0f;
+    float lb, rb, lb2, rb2;
+    warp_window(qkey, qv, e, lb, rb);
+    warp_window(qk2, qv, e, lb2, rb2);
+    for (int s = 0; s < S; ++s) {
+        if constexpr (K2 != 0) {
+            if (!(__ldg(sk2 + 2 * s + 1) > lb2)) continue;
+            if (!(__ldg(sk2 + 2 * s) < rb2)) break;
+        }
+        const int gs = __ldg(spos + s) >> 2, ge = __ldg(spos + s + 1) >> 2;
+        const int g_lo = smem_first_group_above<D>(sm, gs, ge, lb);
+        groups_done += count_range<d, d, Q>(sm, g_lo, ge, lb, rb, qq, e, cz, cyz, cxz);
+    }
+
+    FF acc{0.0f, 0.0f};
+    float acc_abs = 0.0f;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        if (qv[q]) {
+            const int i = qidx[q];
+            const int self = e[q] > 0.0f ? 1 : 0;
+            const int nz = (int)cz[q] - self, nyz = (int)cyz[q] - self, nxz = (int)cxz[q] - self;
+            if (a.counts_out) {
+                int32_t* co = a.counts_out + 3 * I.pt_off;
+                co[i] = nz;
+                co[N + i] = nyz;
+                co[2 * N + i] = nxz;
+            }
+            if (a.eps_out) a.eps_out[I.pt_off + i] = e[q];
+            const float2 p1 = __ldg(a.psi + nz + 1);
+            const float2 p2 = __ldg(a.psi + nyz + 1);
+            const float2 p3 = __ldg(a.psi + nxz + 1);
+            acc = ff_add(acc, p1.x, p1.y);
+            acc = ff_add(acc, -p2.x, -p2.y);
+            acc = ff_add(acc, -p3.x, -p3.y);
+            acc_abs += fabsf(p1.x) + fabsf(p2.x) + fabsf(p3.x);
+        }
+    }
+    double v = (double)acc.hi + (double)acc.lo;
+    double w = (double)acc_abs;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v += __shfl_down_sync(0xffffffffu, v, o);
+        w += __shfl_down_sync(0xffffffffu, w, o);
+    }
+    if (lane == 0) {
+        a.partial[part] = v;
+        a.partial_abs[part] = w;
+        if (a.exec) {
+            const unsigned long long pairs = groups_done * 4ull * (unsigned long long)nvalid;
+            atomicAdd(a.exec, pairs);
+            atomicAdd(a.exec + 1, pairs * 2ull * D);
+        }
+    }
+}
+
 // A whole instance that fits shared memory: staged once in sorted order, then every warp takes
 // blocks of 32*Q queries from a CTA-local counter until none is left (work balances across the
 // warps; the only barriers are at the start and the end of the instance).
@@ -447,18 +635,21 @@ template <int d, int Q, int KS>
 __device__ __forceinline__ void process_instance_sweep_warps(const BatchArgs& a, const InstDesc& I, int wb0,
                                                              float* sm, int* s_wblock) {
     constexpr int D = 1 + 2 * d;
-    const int N = I.N;
+    const int npos = I.npad;  // sorted positions (N, or N plus strip padding)
     const int32_t* sidx = a.sorted_idx + I.sort_off;
-    stage_tile_sorted<d>(I, sidx, 0, N, sm, a.flags);
+    stage_tile_sorted<d>(I, sidx, 0, npos, sm, a.flags);
     if (threadIdx.x == 0) *s_wblock = wb0;
     __syncthreads();
-    const int wb1 = min((N + 32 * Q - 1) / (32 * Q), wb0 + I.wb_chunk);  // this item's warp blocks
+    const int wb1 = min((npos + 32 * Q - 1) / (32 * Q), wb0 + I.wb_chunk);  // this item's warp blocks
     for (;;) {
         int wb = 0;
         if ((threadIdx.x & 31) == 0) wb = atomicAdd(s_wblock, 1);
         wb = __shfl_sync(0xffffffffu, wb, 0);
         if (wb >= wb1) break;
-        sweep_warp_block<d, Q, KS>(a, I, sm, wb, I.part_begin + wb);
+        if (I.strips > 1)
+            sweep_warp_block_strips<d, Q, KS>(a, I, sm, wb, I.part_begin + wb);
+        else
+            sweep_warp_block<d, Q, KS>(a, I, sm, wb, I.part_begin + wb);
     }
     __syncthreads();  // the staged instance stays until every warp is done with it
     (void)D;

@@ -327,3 +327,35 @@ def test_plan_reuse_follows_the_inputs(te_handle):
     o_d = oracle.te_batch([su], w.instances, w.k)
     assert np.max(np.abs(d.cpu().numpy() - o_d)) <= TOL
     assert torch.max(torch.abs(a - e)).item() <= 1e-9
+
+
+@pytest.mark.parametrize("d,R,W,ties", [(1, 1500, 3, False), (1, 2001, 3, True), (2, 1700, 5, False),
+                                        (2, 2731, 3, True), (3, 1100, 4, False)])
+def test_strip_sweep_equals_exhaustive(te_handle, d, R, W, ties):
+    """Resident groups of 4096+ points are cut into strips by a second target coordinate (y_t for
+    d = 1, y_{t'-1-tau} for d >= 2), each padded to groups of four: radii and counts must equal the
+    exhaustive search exactly (ragged strip sizes, many equal keys, several surrogates)."""
+    rng = np.random.default_rng(R + 10 * d)
+    if ties:
+        src = rng.integers(0, 5, (R, 60)).astype(np.float32)
+        tgt = rng.integers(0, 5, (R, 60)).astype(np.float32)
+    else:
+        src, tgt = I.ar2_pair(rng, R, 60)
+    s = I.Series(src, tgt, d=d, tau=2, u=3, perms=I.permutations(rng, 2, R))
+    insts = [I.Instance(0, 20, W, p) for p in (-1, 0, 1)]
+    ds = te.to_device([s])
+    te.te_set_sharing(te_handle, False)
+    try:
+        te.te_set_search(te_handle, False)
+        try:
+            ref = te.te_estimate(te_handle, ds, insts, 4, want_counts=True)
+        finally:
+            te.te_set_search(te_handle, True)
+        got = te.te_estimate(te_handle, ds, insts, 4, want_counts=True)
+        torch.cuda.synchronize()
+        pairs, _, swept = te.te_last_work(te_handle)
+    finally:
+        te.te_set_sharing(te_handle, True)
+    assert swept and pairs < 2 * 3 * (R * W) ** 2
+    assert torch.equal(ref["eps"], got["eps"]) and torch.equal(ref["counts"], got["counts"])
+    assert torch.max(torch.abs(ref["te"] - got["te"])).item() <= 1e-9
