@@ -371,8 +371,7 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
         dhi = std::max(dhi, S.d);
         nmax = std::max(nmax, (int)N);
         dmaxN = std::max(dmaxN, (int)(((N + 3) & ~3) * (1 + 2 * S.d)));
-        const int ns = std::min<int>(te::kMaxStrips, (int)(N / te::kStripPoints));
-        dmaxN_strips = std::max(dmaxN_strips, (int)(((N + 3 * (ns >= 4 ? ns : 0) + 3) & ~3) * (1 + 2 * S.d)));
+        dmaxN_strips = std::max(dmaxN_strips, (int)(((N + 3) & ~3) * (1 + 2 * S.d)));
     }
     P->n_points = off;
     if (dlo != dhi && dhi > kMaxMixedD)
@@ -439,6 +438,7 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
     // its estimates would not be resident on their own either (a resident unshared estimate beats
     // a tiled bundle: the AR(1) scan measured 317 ms unshared vs 450 ms tiled-bundled)
     std::vector<char> bundled(n_inst, 0);
+    std::vector<int> tiled_leaders;  // leaders of bundles too large to stage whole
     if (sweep && h->sharing && !h->per_instance && ks == 5) {
         std::map<std::tuple<const float*, int, int, int, int, int, int>, std::vector<int>> by_target;
         for (int i = 0; i < n_inst; ++i) {
@@ -468,25 +468,23 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
             }
         }
         const int per_b = 32 * te::kBundleQ;
-        const int blockq = te::kBundleThreads * te::kBundleQ;
-        std::vector<WorkItem> titems;
         for (const auto& kv : by_target) {
             const std::vector<int>& v = kv.second;
             const InstDesc& I0 = P->insts[v[0]];
             if (v.size() < 2 || I0.d != P->bd || !shares(I0)) continue;
             const bool resident = resident_bytes(I0) <= kResidentMaxBytes;
-            int nparts_b, chunk = 0;
+            int nparts_b = 0, chunk = 0;
             if (resident) {
                 const int nwb = (I0.N + per_b - 1) / per_b;
                 const int split = std::max(1, std::min(nwb, (want_items + n_bundles - 1) / std::max(1, n_bundles)));
                 chunk = (nwb + split - 1) / split;
                 nparts_b = nwb;
-            } else {
+            } else {  // tiles of at least one strip (kStripPoints) of the bundle
                 const int cols = 1 + I0.d + te::kBundleMax * I0.d;
                 const int budget = I0.d <= 3 ? 72 * 1024 : 110 * 1024;
-                const int cap = std::max(blockq, (budget / (cols * 4)) / blockq * blockq);
+                const int blockq = te::kBundleThreads * te::kBundleQ;
+                const int cap = std::max(te::kStripPoints, (budget / (cols * 4)) / blockq * blockq);
                 P->tsmem = std::max(P->tsmem, (size_t)cap * cols * 4);
-                nparts_b = (I0.N + blockq - 1) / blockq;
             }
             size_t pos = 0;
             while (pos < v.size()) {
@@ -504,22 +502,23 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
                     I.warp_mode = resident ? 1 : 0;
                     I.item_begin = 0;
                     I.n_items = 0;
-                    I.part_begin = n_parts;
-                    I.n_parts = nparts_b;
-                    n_parts += nparts_b;
-                    max_parts = std::max(max_parts, nparts_b);
+                    if (resident) {
+                        I.part_begin = n_parts;
+                        I.n_parts = nparts_b;
+                        n_parts += nparts_b;
+                        max_parts = std::max(max_parts, nparts_b);
+                    }
                 }
                 if (resident) {
                     for (int c = 0; c * chunk < nparts_b; ++c) P->bitems.push_back(WorkItem{v[pos], c * chunk});
                 } else {
-                    for (int c = 0; c < nparts_b; ++c) titems.push_back(WorkItem{v[pos], c * blockq});
+                    tiled_leaders.push_back(v[pos]);  // parts and items once the sort groups are known
                 }
                 pos += nb;
                 ++P->n_bundled;
             }
         }
         P->n_bres = (int)P->bitems.size();
-        P->bitems.insert(P->bitems.end(), titems.begin(), titems.end());
     }
     // warp mode of every unshared estimate: staged whole when it fits shared memory
     for (int i = 0; i < n_inst; ++i) {
@@ -553,20 +552,17 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
             const InstDesc& I0 = P->insts[v[0]];
             const int N = I0.N;
             const int k2lag = I0.d >= 2 ? 1 + I0.tau : 0;
-            int S = std::min(te::kMaxStrips, N / te::kStripPoints);
+            int S = std::min(te::kMaxStrips, (N + te::kStripPoints - 1) / te::kStripPoints);
             int npad = N;
             if (S >= 4) {
-                npad = 0;
-                for (int st = 0; st < S; ++st) {
-                    const int64_t a = ((int64_t)st * N + S - 1) / S, b = ((int64_t)(st + 1) * N + S - 1) / S;
-                    npad += (int)((b - a + 3) & ~3);
-                }
-                for (int i : v) {
+                npad = (S - 1) * te::kStripPoints + ((N - (S - 1) * te::kStripPoints + 3) & ~3);
+                for (int i : v) {  // staged-whole unshared estimates and tiled bundles take strips
                     const InstDesc& I = P->insts[i];
                     const int lag = I.d >= 2 ? 1 + I.tau : 0;
-                    if (bundled[i] || I.warp_mode != 1 || lag != k2lag ||
-                        (int64_t)((npad + 3) & ~3) * (1 + 2 * I.d) > P->smem_floats)
-                        S = 1;
+                    const bool resident_alone = !bundled[i] && I.warp_mode == 1 &&
+                                                (int64_t)((npad + 3) & ~3) * (1 + 2 * I.d) <= P->smem_floats;
+                    const bool tiled_bundle = bundled[i] && I.warp_mode == 0;
+                    if (lag != k2lag || !(resident_alone || tiled_bundle)) S = 1;
                 }
             }
             if (S < 4) {
@@ -587,6 +583,22 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
             if (S > 1) strip_total += S + 1;
         }
         P->strip_total = strip_total;
+    }
+    // tiled bundles: one work item per block of kBundleThreads * kBundleQ sorted positions
+    {
+        const int blockq = te::kBundleThreads * te::kBundleQ;
+        for (int leader : tiled_leaders) {
+            const InstDesc& L = P->insts[leader];
+            const int nparts_b = (L.npad + blockq - 1) / blockq;
+            for (int m = 0; m < L.bundle_n; ++m) {
+                InstDesc& I = P->insts[P->members[L.bundle_off + m]];
+                I.part_begin = n_parts;
+                I.n_parts = nparts_b;
+                n_parts += nparts_b;
+                max_parts = std::max(max_parts, nparts_b);
+            }
+            for (int c = 0; c < nparts_b; ++c) P->bitems.push_back(WorkItem{leader, c * blockq});
+        }
     }
     // work items of the unshared estimates (cost order, an estimate's items contiguous) and their
     // partial-sum ranges: a staged-whole estimate is cut into items of warp blocks (32 * qpt

@@ -39,8 +39,8 @@ __device__ __forceinline__ void stage_bundle(const BatchArgs& a, const InstDesc&
     const int N = nv;
     const int nfill = (N + 3) & ~3;
     for (int p = threadIdx.x; p < nfill; p += blockDim.x) {
-        if (p < N) {
-            const int i = __ldg(sidx + base + p);
+        const int i = p < N ? __ldg(sidx + base + p) : -1;  // -1: strip padding
+        if (i >= 0) {
             const int r = i / L.W;
             const int t = L.t_start + (i - r * L.W);
             const float* y = L.tgt + (size_t)r * L.T;
@@ -60,8 +60,8 @@ __device__ __forceinline__ void stage_bundle(const BatchArgs& a, const InstDesc&
         const int u = J.u, R = J.R;
         float* col = sm + cap * (DA + m * d);
         for (int p = threadIdx.x; p < nfill; p += blockDim.x) {
-            if (p < N) {
-                const int i = __ldg(sidx + base + p);
+            const int i = p < N ? __ldg(sidx + base + p) : -1;
+            if (i >= 0) {
                 const int r = i / L.W;
                 const int t = L.t_start + (i - r * L.W);
                 int rs = r;
@@ -557,6 +557,251 @@ __device__ __forceinline__ void bundle_item_tiled(const BatchArgs& a, const Inst
     }
 }
 
+// bundle_item_tiled for a bundle whose sort group is cut into strips (SortGroup; strips start at
+// multiples of kStripPoints, so the CTA's query block lies in one strip, and a strip fits one tile).
+// Pass 1: the own strip staged whole and swept outward from each warp's queries, then the other
+// strips nearest first in the second key (coordinate K2: y_{t'-1-tau} for d >= 2, y_t for d = 1)
+// while their key range meets the CTA's window, each staged over the CTA's y_{t'-1} window.
+// Pass 2: the y_{t'-1} window of every strip (for d >= 2 only those meeting the second-key
+// window: y_t bounds neither n_z nor n_xz). Skips are exact as in sweep_warp_block_strips.
+template <int d, int Q, int KS, int M>
+__device__ __forceinline__ void bundle_item_tiled_strips(const BatchArgs& a, const InstDesc& L, const int32_t* mem,
+                                                         int nb, int q0, int item, float* sm, double* sred,
+                                                         float* sbnd) {
+    constexpr int DA = 1 + d;
+    constexpr int D = 1 + 2 * d;
+    constexpr int K2 = d >= 2 ? 2 : 0;
+    const int N = L.N;
+    const int npos = L.npad;
+    const int S = L.strips;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int32_t* sidx = a.sorted_idx + L.sort_off;
+    const float* skey = a.sorted_key + L.sort_off;
+    const int32_t* spos = a.strip_pos + L.strip_off;
+    const float* sk2 = a.strip_k2 + 2 * L.strip_off;
+    const int block = blockDim.x * Q;
+    const int cap = ((a.smem_floats / (DA + M * d)) / block) * block;  // >= kStripPoints (the plan)
+    int coff[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) coff[m] = cap * (DA + min(m, nb - 1) * d);
+
+    const int wbase = q0 + warp * 32 * Q;
+    u64 qa[Q][DA];
+    u64 qc[M][Q][d];
+    float qkey[Q], qk2[Q];
+    int qidx[Q];
+    bool qv[Q];
+    int nvalid = 0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int pos = wbase + q * 32 + lane;
+        qidx[q] = pos < npos ? __ldg(sidx + pos) : -1;
+        qv[q] = qidx[q] >= 0;
+        const int ii = qv[q] ? qidx[q] : 0;
+        const int r = ii / L.W;
+        const int tt = L.t_start + (ii - r * L.W);
+        const float* y = L.tgt + (size_t)r * L.T;
+        float pa[DA];
+        pa[0] = qv[q] ? __ldg(y + tt) : 0.0f;
+#pragma unroll
+        for (int c = 0; c < d; ++c) pa[1 + c] = qv[q] ? __ldg(y + tt - 1 - c * L.tau) : 0.0f;
+#pragma unroll
+        for (int c = 0; c < DA; ++c) qa[q][c] = dup2(pa[c]);
+        qkey[q] = pa[1];
+        qk2[q] = pa[K2];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const InstDesc& J = a.insts[mem[min(m, nb - 1)]];
+            int rs = r;
+            if (J.perm && qv[q]) {
+                rs = __ldg(J.perm + r);
+                if ((unsigned)rs >= (unsigned)J.R) {
+                    atomicOr(a.flags, kFlagBadPerm);
+                    rs = 0;
+                }
+            }
+            const float* x = J.src + (size_t)rs * L.T;
+#pragma unroll
+            for (int c = 0; c < d; ++c) qc[m][q][c] = dup2(qv[q] ? __ldg(x + tt - J.u - c * L.tau) : 0.0f);
+        }
+        nvalid += __popc(__ballot_sync(0xffffffffu, qv[q]));
+    }
+    const bool warp_active = nvalid > 0;
+    unsigned long long groups_done = 0;
+
+    int st_base = -1, st_n = 0;
+    auto stage = [&](int base, int n) {  // sorted positions base .. base + n - 1 as one tile
+        if (st_base == base && st_n == n) return;
+        __syncthreads();
+        stage_bundle<d, M>(a, L, mem, nb, sidx, base, n, cap, sm);
+        __syncthreads();
+        st_base = base;
+        st_n = n;
+    };
+
+    float t[M][Q][KS];
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int s = 0; s < KS; ++s) t[m][q][s] = f_inf();
+
+    // ---- pass 1, own strip: staged whole, each warp outward from its queries
+    const int s0 = q0 / kStripPoints;
+    {
+        const int ps = __ldg(spos + s0), pe = __ldg(spos + s0 + 1);
+        stage(ps, pe - ps);
+        if (warp_active) {
+            const int ng = (pe - ps + 3) >> 2;
+            const int g_own0 = (wbase - ps) >> 2;
+            const int g_own1 = min(ng, (min(wbase + 32 * Q, pe) - ps + 3) >> 2);
+            bool done = false;
+            groups_done += bknn_range<d, Q, KS, M>(sm, coff, g_own0, g_own1, 0, qa, qc, qkey, qv, t, done);
+            done = false;
+            groups_done += bknn_range<d, Q, KS, M>(sm, coff, g_own1, ng, +1, qa, qc, qkey, qv, t, done);
+            done = false;
+            groups_done += bknn_range<d, Q, KS, M>(sm, coff, 0, g_own0, -1, qa, qc, qkey, qv, t, done);
+        }
+    }
+    // ---- pass 1, other strips nearest first in the second key
+    bool up = s0 + 1 < S, down = s0 > 0;
+    for (int step = 1; up || down; ++step) {
+        for (int side = 0; side < 2; ++side) {
+            const int s = side == 0 ? s0 + step : s0 - step;
+            if (side == 0 ? (!up || s >= S) : (!down || s < 0)) {
+                if (side == 0) up = false;
+                else down = false;
+                continue;
+            }
+            float r[Q], lb, rb, lb2, rb2;
+            bundle_radii<Q, KS, M>(t, r);
+            warp_window(qkey, qv, r, lb, rb);
+            warp_window(qk2, qv, r, lb2, rb2);
+            float blb2 = lb2, brb2 = rb2;
+            block_minmax(blb2, brb2, sbnd);
+            if (side == 0 && !(__ldg(sk2 + 2 * s) < brb2)) {
+                up = false;
+                continue;
+            }
+            if (side == 1 && !(__ldg(sk2 + 2 * s + 1) > blb2)) {
+                down = false;
+                continue;
+            }
+            float blb = lb, brb = rb;
+            block_minmax(blb, brb, sbnd);
+            const int ps = __ldg(spos + s), len = __ldg(spos + s + 1) - ps;
+            const int plo = ps + first_greater(skey + ps, len, blb);
+            const int phi = ps + first_not_less(skey + ps, len, brb);
+            if (plo >= phi) continue;
+            stage(plo, phi - plo);
+            if (warp_active) {
+                const int ng = (phi - plo + 3) >> 2;
+                int g = 0;
+                while (g < ng && group_key_hi<DA>(sm, g) <= lb) ++g;
+                bool done = false;
+                groups_done += bknn_range<d, Q, KS, M>(sm, coff, g, ng, +1, qa, qc, qkey, qv, t, done);
+            }
+        }
+    }
+    float e[M][Q], emax[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        emax[q] = 0.0f;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            e[m][q] = topk_select(t[m][q], a.k);
+            emax[q] = fmaxf(emax[q], e[m][q]);
+        }
+    }
+
+    // ---- pass 2
+    float cz[M][Q], cyz[M][Q], cxz[M][Q];
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) cz[m][q] = cyz[m][q] = cxz[m][q] = 0.0f;
+    float lb, rb, lb2, rb2;
+    warp_window(qkey, qv, emax, lb, rb);
+    warp_window(qk2, qv, emax, lb2, rb2);
+    float blb = lb, brb = rb, blb2 = lb2, brb2 = rb2;
+    block_minmax(blb, brb, sbnd);
+    block_minmax(blb2, brb2, sbnd);
+    for (int s = 0; s < S; ++s) {
+        if constexpr (K2 != 0) {
+            if (!(__ldg(sk2 + 2 * s + 1) > blb2)) continue;
+            if (!(__ldg(sk2 + 2 * s) < brb2)) break;
+        }
+        const int ps = __ldg(spos + s), len = __ldg(spos + s + 1) - ps;
+        const int plo = ps + first_greater(skey + ps, len, blb);
+        const int phi = ps + first_not_less(skey + ps, len, brb);
+        if (plo >= phi) continue;
+        stage(plo, phi - plo);
+        if (warp_active) {
+            const int ng = (phi - plo + 3) >> 2;
+            int g = 0;
+            while (g < ng && group_key_hi<DA>(sm, g) <= lb) ++g;
+            groups_done += bcount_range<d, Q, M>(sm, coff, g, ng, lb, rb, qa, qc, e, cz, cyz, cxz);
+        }
+    }
+
+    // ---- per member: digamma terms of Eq. 9, FP64 partial per CTA block
+#pragma unroll 1
+    for (int m = 0; m < nb; ++m) {
+        const InstDesc& J = a.insts[mem[m]];
+        const int64_t pt_off = J.pt_off;
+        FF acc{0.0f, 0.0f};
+        float acc_abs = 0.0f;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            float em = e[0][q], cm = cz[0][q], cym = cyz[0][q], cxm = cxz[0][q];
+#pragma unroll
+            for (int mm = 1; mm < M; ++mm)
+                if (mm == m) {
+                    em = e[mm][q];
+                    cm = cz[mm][q];
+                    cym = cyz[mm][q];
+                    cxm = cxz[mm][q];
+                }
+            if (qv[q]) {
+                const int i = qidx[q];
+                const int self = em > 0.0f ? 1 : 0;
+                const int nz = (int)cm - self, nyz = (int)cym - self, nxz = (int)cxm - self;
+                if (a.counts_out) {
+                    int32_t* co = a.counts_out + 3 * pt_off;
+                    co[i] = nz;
+                    co[N + i] = nyz;
+                    co[2 * N + i] = nxz;
+                }
+                if (a.eps_out) a.eps_out[pt_off + i] = em;
+                const float2 p1 = __ldg(a.psi + nz + 1);
+                const float2 p2 = __ldg(a.psi + nyz + 1);
+                const float2 p3 = __ldg(a.psi + nxz + 1);
+                acc = ff_add(acc, p1.x, p1.y);
+                acc = ff_add(acc, -p2.x, -p2.y);
+                acc = ff_add(acc, -p3.x, -p3.y);
+                acc_abs += fabsf(p1.x) + fabsf(p2.x) + fabsf(p3.x);
+            }
+        }
+        double v = (double)acc.hi + (double)acc.lo;
+        double w = (double)acc_abs;
+        __syncthreads();  // sred of the previous member is read
+        block_sum2(v, w, sred);
+        if (threadIdx.x == 0) {
+            a.partial[J.part_begin + item] = v;
+            a.partial_abs[J.part_begin + item] = w;
+        }
+    }
+    if (a.exec && warp_active && lane == 0) {
+        const unsigned long long g4 = groups_done * 4ull * (unsigned long long)nvalid;
+        const unsigned long long alg = g4 * (unsigned long long)nb * 2ull * D;
+        const unsigned long long run = g4 * (2ull * DA + (unsigned long long)M * 2ull * d);
+        atomicAdd(a.exec, g4 * (unsigned long long)nb);
+        atomicAdd(a.exec + 1, alg);
+        atomicAdd(a.exec + 2, alg > run ? alg - run : 0ull);
+    }
+}
+
 // The bundle kernel: a CTA takes a bundle (its leader's work item) from the queue, stages it,
 // and its warps take 32*Q-query blocks from a CTA-local counter; TILED: bundles too large to stage
 // whole, one CTA query block per work item (a separate instantiation, so that the resident path
@@ -580,7 +825,11 @@ __global__ void __launch_bounds__(kBundleThreads, d <= 3 ? 3 : 2) bundle_kernel(
         const int32_t* mem = a.members + L.bundle_off;
         const int nb = L.bundle_n;
         if constexpr (TILED) {  // too large to stage whole: CTA tiles around a block of queries
-            bundle_item_tiled<d, Q, KS, M>(a, L, mem, nb, w.q0, w.q0 / (int)(blockDim.x * Q), sm, sred, sbnd);
+            const int item = w.q0 / (int)(blockDim.x * Q);
+            if (L.strips > 1)
+                bundle_item_tiled_strips<d, Q, KS, M>(a, L, mem, nb, w.q0, item, sm, sred, sbnd);
+            else
+                bundle_item_tiled<d, Q, KS, M>(a, L, mem, nb, w.q0, item, sm, sred, sbnd);
             continue;
         } else {
             (void)sred;

@@ -34,11 +34,13 @@ struct InstDesc {
 // Points of one (series, window start, window) group: the estimates of a group (original and
 // surrogates) share the target coordinates, so they share one order of the points sorted by the
 // target coordinate y_{t'-1} (coordinate 1 of the joint space). With S > 1 strips the points are
-// first cut by a second target coordinate y_{t'-k2lag} into S strips of equal count, each sorted
-// by y_{t'-1} and padded to a multiple of four positions (index -1, key +inf), so that a 4-point
-// group never spans two strips; strip s holds positions strip_pos[s] .. strip_pos[s+1]-1 and its
-// second-key values lie in [strip_k2[2s], strip_k2[2s+1]]. The second key is y_{t'-1-tau}
-// (coordinate 2, in y-) for d >= 2 and y_t (coordinate 0, not in y-) for d = 1.
+// first ordered by a second target coordinate y_{t'-k2lag} and cut into strips of kStripPoints
+// consecutive ranks (the last one shorter, padded to a multiple of four positions with index -1
+// and key +inf), each sorted by y_{t'-1}; strip s holds positions strip_pos[s] = s * kStripPoints
+// .. strip_pos[s+1]-1 and its second-key values lie in [strip_k2[2s], strip_k2[2s+1]]. Strip
+// starts are multiples of 1024, so no warp block (32 Q) or 256-query CTA block spans two strips.
+// The second key is y_{t'-1-tau} (coordinate 2, in y-) for d >= 2 and y_t (coordinate 0, not in
+// y-) for d = 1.
 struct SortGroup {
     const float* tgt;
     int32_t R, T, W, t_start, N;
@@ -50,7 +52,7 @@ struct SortGroup {
                            // 2 strip_off + 2 S - 1]
 };
 
-constexpr int kStripPoints = 1024;  // target points per strip
+constexpr int kStripPoints = 1024;  // points per strip (a multiple of 256 and of 32 * Q)
 constexpr int kMaxStrips = 64;
 
 // Largest point count the sweep mode sorts (one CTA per group; runs in shared memory, merges

@@ -5,10 +5,11 @@
 // double the run length through global memory (each thread merges its share of the output after a
 // merge-path search for its starting split).
 //   S == 1: key = y_{t'-1} (coordinate 1 of the joint space).
-//   S > 1 (strips): first sorted by the second key y_{t'-k2lag} and cut into S strips of equal
-//           count, then sorted by (strip, y_{t'-1}); strip s is written at positions
-//           strip_pos[s] .. strip_pos[s+1]-1, padded to a multiple of four with (index -1, key
-//           +inf), and the lowest and highest second key of its points are recorded.
+//   S > 1 (strips): first sorted by the second key y_{t'-k2lag} and cut into strips of
+//           kStripPoints consecutive ranks (the last one shorter), then sorted by (strip, y_{t'-1});
+//           strip s is written at positions s * kStripPoints .. (the last strip padded to a
+//           multiple of four with (index -1, key +inf)), and the lowest and highest second key of
+//           its points are recorded.
 // Keys are FP32 values mapped to unsigned integers that order like the floats.
 #include "te_internal.h"
 
@@ -170,13 +171,14 @@ __global__ void __launch_bounds__(kSortThreads) sort_groups_kernel(const SortGro
         return;
     }
     const int S = G.S;
-    // 1. by the second key: strip s holds the points of rank ceil(s N / S) .. ceil((s+1) N / S) - 1
+    const int L = kStripPoints;
+    // 1. by the second key: strip s holds the points of rank s L .. min((s + 1) L, N) - 1
     sort_pairs(N, [&](int p, u64k& k, int& i) { k = ord_bits(group_coord(G, p, G.k2lag)); i = p; }, ak, ai, bk,
                bi, sk, si);
     if (threadIdx.x == 0) {
         int pos = 0;
         for (int s = 0; s < S; ++s) {
-            const int a = (int)(((long long)s * N + S - 1) / S), b = (int)(((long long)(s + 1) * N + S - 1) / S);
+            const int a = s * L, b = min((s + 1) * L, N);
             s_pos[s] = pos;
             strip_k2[2 * G.strip_off + 2 * s] = from_ord((unsigned)ak[a]);
             strip_k2[2 * G.strip_off + 2 * s + 1] = from_ord((unsigned)ak[b - 1]);
@@ -191,7 +193,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_groups_kernel(const SortGro
         N,
         [&](int p, u64k& k, int& i) {
             i = ai[p];
-            const unsigned s = (unsigned)(((long long)p * S) / N);
+            const unsigned s = (unsigned)(p / L);
             k = ((u64k)s << 32) | ord_bits(group_coord(G, i, 1));
         },
         ak, ai, bk, bi, sk, si);
@@ -203,8 +205,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_groups_kernel(const SortGro
     __syncthreads();
     for (int p = threadIdx.x; p < N; p += blockDim.x) {
         const int s = (int)(ak[p] >> 32);
-        const int a = (int)(((long long)s * N + S - 1) / S);
-        const int dst = s_pos[s] + (p - a);
+        const int dst = s_pos[s] + (p - s * L);
         out_idx[G.off + dst] = ai[p];
         out_key[G.off + dst] = from_ord((unsigned)ak[p]);
     }

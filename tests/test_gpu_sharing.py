@@ -166,3 +166,25 @@ def test_delay_scan_with_tiled_bundles(te_handle):
     te.te_delay_scan(te_handle, dsa[0], wa.t_starts[0], wa.window, 8, 10, wa.S, wa.k)
     torch.cuda.synchronize()
     assert te.te_last_alu_ops(te_handle)[1] == 0
+
+
+@pytest.mark.parametrize("d,ties", [(1, False), (1, True), (2, True)])
+def test_tiled_bundles_with_strips_equal_unshared(te_handle, d, ties):
+    """Tiled bundles over sort groups cut into strips (second key y_t for d = 1, which prunes only
+    the kNN pass; y_{t'-1-tau} for d >= 2, which prunes both passes): radii and counts equal the
+    unshared search, many equal keys included."""
+    rng = np.random.default_rng(77 + d + (10 if ties else 0))
+    R, W = 5000, 4  # 20,000 points: too large to stage whole even alone
+    if ties:
+        src = rng.integers(0, 6, (R, 40)).astype(np.float32)
+        tgt = rng.integers(0, 6, (R, 40)).astype(np.float32)
+    else:
+        src, tgt = I.ar2_pair(rng, R, 40)
+    s = I.Series(src, tgt, d=d, tau=2, u=3, perms=I.permutations(rng, 4, R))
+    insts = [I.Instance(0, 15, W, p) for p in (-1, 0, 1, 2, 3)]
+    ds = te.to_device([s])
+    off, b0, _, _, _ = _estimate(te_handle, ds, insts, 4, False)
+    on, b1, _, _, _ = _estimate(te_handle, ds, insts, 4, True)
+    assert b0 == 0 and b1 == 2
+    assert torch.equal(off["counts"], on["counts"]) and torch.equal(off["eps"], on["eps"])
+    assert torch.max(torch.abs(off["te"] - on["te"])).item() <= 1e-12
