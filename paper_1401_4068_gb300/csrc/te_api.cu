@@ -556,13 +556,16 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
             int npad = N;
             if (S >= 4) {
                 npad = (S - 1) * te::kStripPoints + ((N - (S - 1) * te::kStripPoints + 3) & ~3);
-                for (int i : v) {  // staged-whole unshared estimates and tiled bundles take strips
+                for (int i : v) {  // staged-whole unshared estimates, tiled bundles and tiled
+                                   // estimates whose CTA block divides a strip take strips
                     const InstDesc& I = P->insts[i];
                     const int lag = I.d >= 2 ? 1 + I.tau : 0;
                     const bool resident_alone = !bundled[i] && I.warp_mode == 1 &&
                                                 (int64_t)((npad + 3) & ~3) * (1 + 2 * I.d) <= P->smem_floats;
                     const bool tiled_bundle = bundled[i] && I.warp_mode == 0;
-                    if (lag != k2lag || !(resident_alone || tiled_bundle)) S = 1;
+                    const bool tiled_alone = !bundled[i] && I.warp_mode == 0 && te::kStripPoints % per == 0 &&
+                                             (int64_t)te::kStripPoints * (1 + 2 * I.d) * 4 <= kSweepSmemMaxBytes;
+                    if (lag != k2lag || !(resident_alone || tiled_bundle || tiled_alone)) S = 1;
                 }
             }
             if (S < 4) {
@@ -578,6 +581,9 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
                 I.strips = S;
                 I.npad = npad;
                 I.strip_off = G.strip_off;
+                // a tiled estimate over strips stages a whole strip per tile
+                if (S > 1 && !bundled[i] && I.warp_mode == 0)
+                    P->smem_floats = std::max(P->smem_floats, te::kStripPoints * (1 + 2 * I.d));
             }
             P->sorted_total += npad;
             if (S > 1) strip_total += S + 1;
@@ -616,7 +622,7 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
             I.n_parts = nwb;
             for (int m = 0; m < I.n_items; ++m) P->items.push_back(WorkItem{i, m * I.wb_chunk});
         } else {
-            I.n_items = (I.N + per - 1) / per;
+            I.n_items = (I.npad + per - 1) / per;
             I.n_parts = I.n_items;
             for (int m = 0; m < I.n_items; ++m) P->items.push_back(WorkItem{i, m * per});
         }
@@ -624,6 +630,7 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
         max_parts = std::max(max_parts, I.n_parts);
     }
     P->n_parts = n_parts;
+    P->smem = (size_t)P->smem_floats * sizeof(float);
     // every unshared estimate staged whole with one d <= 2: the warp-mode sweep kernel (1024-thread
     // CTAs unless a shape was set or tuned for this signature)
     bool all_warp = !P->items.empty();

@@ -30,6 +30,8 @@ __global__ void __launch_bounds__(kBatchedMaxThreads) batched_kernel(const Batch
         if constexpr (SWEEP) {                                                            \
             if (I.warp_mode)                                                              \
                 process_instance_sweep_warps<DD, Q, KS>(a, I, w.q0, sm, &s_wblock);       \
+            else if (I.strips > 1)                                                        \
+                process_item_sweep_strips<DD, Q, KS>(a, I, w.q0, part, sm, sred, sbnd);   \
             else                                                                          \
                 process_item_sweep<DD, Q, KS>(a, I, w.q0, part, sm, sred, sbnd);          \
         } else {                                                                          \

@@ -441,6 +441,192 @@ __device__ __forceinline__ void sweep_warp_block(const BatchArgs& a, const InstD
     }
 }
 
+// process_item_sweep for an estimate whose sort group is cut into strips (SortGroup): the CTA's
+// query block (a divisor of kStripPoints, so it lies in one strip) first sweeps its own strip,
+// staged whole, outward from each warp's queries, then the other strips nearest first in the
+// second key (coordinate K2: y_{t'-1-tau} for d >= 2, y_t for d = 1) while their key range meets
+// the CTA's window, each staged over the CTA's y_{t'-1} window; pass 2 stages the y_{t'-1} window
+// of every strip (d >= 2: of those meeting the second-key window). Skips are exact as in
+// sweep_warp_block_strips. A tile holds at least one strip (the plan).
+template <int d, int Q, int KS>
+__device__ __forceinline__ void process_item_sweep_strips(const BatchArgs& a, const InstDesc& I, int q0, int it,
+                                                          float* sm, double* sred, float* sbnd) {
+    constexpr int D = 1 + 2 * d;
+    constexpr int K2 = d >= 2 ? 2 : 0;
+    const int N = I.N;
+    const int npos = I.npad;
+    const int S = I.strips;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int32_t* sidx = a.sorted_idx + I.sort_off;
+    const float* skey = a.sorted_key + I.sort_off;
+    const int32_t* spos = a.strip_pos + I.strip_off;
+    const float* sk2 = a.strip_k2 + 2 * I.strip_off;
+    const int wbase = q0 + warp * 32 * Q;
+    u64 qq[Q][D];
+    float qkey[Q], qk2[Q];
+    int qidx[Q];
+    bool qv[Q];
+    int nvalid = 0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int pos = wbase + q * 32 + lane;
+        qidx[q] = pos < npos ? __ldg(sidx + pos) : -1;
+        qv[q] = qidx[q] >= 0;
+        float p[D];
+        if (qv[q]) {
+            gather_point<d>(I, qidx[q], p, a.flags);
+        } else {
+#pragma unroll
+            for (int c = 0; c < D; ++c) p[c] = 0.0f;
+        }
+        qkey[q] = p[1];
+        qk2[q] = p[K2];
+#pragma unroll
+        for (int c = 0; c < D; ++c) qq[q][c] = dup2(p[c]);
+        nvalid += __popc(__ballot_sync(0xffffffffu, qv[q]));
+    }
+    const bool warp_active = nvalid > 0;
+    unsigned long long groups_done = 0;
+
+    int st_base = -1, st_n = 0;
+    auto stage = [&](int base, int n) {  // sorted positions base .. base + n - 1 as one tile
+        if (st_base == base && st_n == n) return;
+        __syncthreads();
+        stage_tile_sorted<d>(I, sidx, base, n, sm, a.flags);
+        __syncthreads();
+        st_base = base;
+        st_n = n;
+    };
+
+    float t[Q][KS];
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int m = 0; m < KS; ++m) t[q][m] = f_inf();
+    const int s0 = q0 / kStripPoints;
+    {
+        const int ps = __ldg(spos + s0), pe = __ldg(spos + s0 + 1);
+        stage(ps, pe - ps);
+        if (warp_active) {
+            const int ng = (pe - ps + 3) >> 2;
+            const int g_own0 = (wbase - ps) >> 2;
+            const int g_own1 = min(ng, (min(wbase + 32 * Q, pe) - ps + 3) >> 2);
+            bool done = false;
+            groups_done += knn_range<D, Q, KS>(sm, g_own0, g_own1, 0, qq, qkey, qv, t, done);
+            done = false;
+            groups_done += knn_range<D, Q, KS>(sm, g_own1, ng, +1, qq, qkey, qv, t, done);
+            done = false;
+            groups_done += knn_range<D, Q, KS>(sm, 0, g_own0, -1, qq, qkey, qv, t, done);
+        }
+    }
+    bool up = s0 + 1 < S, down = s0 > 0;
+    for (int step = 1; up || down; ++step) {
+        for (int side = 0; side < 2; ++side) {
+            const int s = side == 0 ? s0 + step : s0 - step;
+            if (side == 0 ? (!up || s >= S) : (!down || s < 0)) {
+                if (side == 0) up = false;
+                else down = false;
+                continue;
+            }
+            float r[Q], lb, rb, lb2, rb2;
+            current_radii(t, r);
+            warp_window(qkey, qv, r, lb, rb);
+            warp_window(qk2, qv, r, lb2, rb2);
+            float blb2 = lb2, brb2 = rb2;
+            block_minmax(blb2, brb2, sbnd);
+            if (side == 0 && !(__ldg(sk2 + 2 * s) < brb2)) {
+                up = false;
+                continue;
+            }
+            if (side == 1 && !(__ldg(sk2 + 2 * s + 1) > blb2)) {
+                down = false;
+                continue;
+            }
+            float blb = lb, brb = rb;
+            block_minmax(blb, brb, sbnd);
+            const int ps = __ldg(spos + s), len = __ldg(spos + s + 1) - ps;
+            const int plo = ps + first_greater(skey + ps, len, blb);
+            const int phi = ps + first_not_less(skey + ps, len, brb);
+            if (plo >= phi) continue;
+            stage(plo, phi - plo);
+            if (warp_active) {
+                const int ng = (phi - plo + 3) >> 2;
+                int g = 0;
+                while (g < ng && group_key_hi<D>(sm, g) <= lb) ++g;
+                bool done = false;
+                groups_done += knn_range<D, Q, KS>(sm, g, ng, +1, qq, qkey, qv, t, done);
+            }
+        }
+    }
+    float e[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) e[q] = topk_select(t[q], a.k);
+
+    float cz[Q], cyz[Q], cxz[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) cz[q] = cyz[q] = cxz[q] = 0.0f;
+    float lb, rb, lb2, rb2;
+    warp_window(qkey, qv, e, lb, rb);
+    warp_window(qk2, qv, e, lb2, rb2);
+    float blb = lb, brb = rb, blb2 = lb2, brb2 = rb2;
+    block_minmax(blb, brb, sbnd);
+    block_minmax(blb2, brb2, sbnd);
+    for (int s = 0; s < S; ++s) {
+        if constexpr (K2 != 0) {
+            if (!(__ldg(sk2 + 2 * s + 1) > blb2)) continue;
+            if (!(__ldg(sk2 + 2 * s) < brb2)) break;
+        }
+        const int ps = __ldg(spos + s), len = __ldg(spos + s + 1) - ps;
+        const int plo = ps + first_greater(skey + ps, len, blb);
+        const int phi = ps + first_not_less(skey + ps, len, brb);
+        if (plo >= phi) continue;
+        stage(plo, phi - plo);
+        if (warp_active) {
+            const int ng = (phi - plo + 3) >> 2;
+            int g = 0;
+            while (g < ng && group_key_hi<D>(sm, g) <= lb) ++g;
+            groups_done += count_range<d, d, Q>(sm, g, ng, lb, rb, qq, e, cz, cyz, cxz);
+        }
+    }
+
+    FF acc{0.0f, 0.0f};
+    float acc_abs = 0.0f;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        if (qv[q]) {
+            const int i = qidx[q];
+            const int self = e[q] > 0.0f ? 1 : 0;
+            const int nz = (int)cz[q] - self, nyz = (int)cyz[q] - self, nxz = (int)cxz[q] - self;
+            if (a.counts_out) {
+                int32_t* co = a.counts_out + 3 * I.pt_off;
+                co[i] = nz;
+                co[N + i] = nyz;
+                co[2 * N + i] = nxz;
+            }
+            if (a.eps_out) a.eps_out[I.pt_off + i] = e[q];
+            const float2 p1 = __ldg(a.psi + nz + 1);
+            const float2 p2 = __ldg(a.psi + nyz + 1);
+            const float2 p3 = __ldg(a.psi + nxz + 1);
+            acc = ff_add(acc, p1.x, p1.y);
+            acc = ff_add(acc, -p2.x, -p2.y);
+            acc = ff_add(acc, -p3.x, -p3.y);
+            acc_abs += fabsf(p1.x) + fabsf(p2.x) + fabsf(p3.x);
+        }
+    }
+    if (a.exec && warp_active && lane == 0) {
+        const unsigned long long pairs = groups_done * 4ull * (unsigned long long)nvalid;
+        atomicAdd(a.exec, pairs);
+        atomicAdd(a.exec + 1, pairs * 2ull * D);
+    }
+    double v = (double)acc.hi + (double)acc.lo;
+    double w = (double)acc_abs;
+    block_sum2(v, w, sred);
+    if (threadIdx.x == 0) {
+        a.partial[it] = v;
+        a.partial_abs[it] = w;
+    }
+}
+
 // first group g in [g0, g1) of a staged tile with group_key_hi(g) > x (keys ascending in range)
 template <int D>
 __device__ __forceinline__ int smem_first_group_above(const float* __restrict__ s, int g0, int g1, float x) {

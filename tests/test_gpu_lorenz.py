@@ -159,3 +159,58 @@ def test_paper_chunk_sweep_equals_exhaustive(te_handle):
     torch.cuda.synchronize()
     assert te.te_last_work(te_handle)[2]
     assert torch.equal(ref["eps"], got["eps"]) and torch.equal(ref["counts"], got["counts"])
+
+
+@pytest.mark.parametrize("shape", [(256, 1), (512, 1)])
+def test_paper_chunk_strips_equal_exhaustive(te_handle, shape):
+    """With a CTA block that divides a strip, the unshared tiled sweep of the 17-D chunk runs over
+    strips (second key y_{t'-1-tau}); radii and counts equal the exhaustive search."""
+    w = I.paper_chunk(chunks=2)
+    ds = te.to_device(w.series)
+    te.te_set_search(te_handle, False)
+    try:
+        ref = te.te_estimate(te_handle, ds, w.instances, w.k, want_counts=True)
+    finally:
+        te.te_set_search(te_handle, True)
+    te.te_set_launch_config(te_handle, *shape)
+    try:
+        got = te.te_estimate(te_handle, ds, w.instances, w.k, want_counts=True)
+        torch.cuda.synchronize()
+        pairs, _, swept = te.te_last_work(te_handle)
+    finally:
+        te.te_set_launch_config(te_handle, 0, 0)
+    N = w.n_points(w.instances[0])
+    assert swept and pairs < 0.25 * 2 * 2 * N * N
+    assert torch.equal(ref["eps"], got["eps"]) and torch.equal(ref["counts"], got["counts"])
+
+
+@pytest.mark.parametrize("N,W,ties", [(20000, 4, True), (40961, 13, False)])
+def test_tiled_strips_equal_exhaustive(te_handle, N, W, ties):
+    """Unshared estimates too large to stage whole (d = 2), CTA blocks of 256 queries: the tiled
+    sweep over strips equals the exhaustive search, many equal keys included."""
+    rng = np.random.default_rng(N + 5)
+    R = N // W
+    if ties:
+        src = rng.integers(0, 6, (R, 40)).astype(np.float32)
+        tgt = rng.integers(0, 6, (R, 40)).astype(np.float32)
+    else:
+        src = rng.standard_normal((R, 40)).astype(np.float32)
+        tgt = rng.standard_normal((R, 40)).astype(np.float32)
+    s = I.Series(src, tgt, d=2, tau=1, u=3, perms=I.permutations(rng, 1, R))
+    insts = [I.Instance(0, 10, W, -1), I.Instance(0, 10, W, 0)]
+    ds = te.to_device([s])
+    te.te_set_sharing(te_handle, False)
+    try:
+        te.te_set_search(te_handle, False)
+        try:
+            ref = te.te_estimate(te_handle, ds, insts, 4, want_counts=True)
+        finally:
+            te.te_set_search(te_handle, True)
+        te.te_set_launch_config(te_handle, 128, 2)
+        got = te.te_estimate(te_handle, ds, insts, 4, want_counts=True)
+        torch.cuda.synchronize()
+    finally:
+        te.te_set_launch_config(te_handle, 0, 0)
+        te.te_set_sharing(te_handle, True)
+    assert torch.equal(ref["eps"], got["eps"]) and torch.equal(ref["counts"], got["counts"])
+    assert torch.max(torch.abs(ref["te"] - got["te"])).item() <= 1e-9
