@@ -531,8 +531,7 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
         I.warp_mode = (sweep && fits && !h->per_instance) ? 1 : 0;
     }
     // sort groups: one per (target series, repetitions, window start, window); a group whose every
-    // estimate is staged whole and unshared and that agrees on the second key is cut into strips
-    // (about kStripPoints points each, at least 4) when the padded positions still fit
+    // estimate takes a strip-aware path and agrees on the second key is cut into strips
     if (sweep) {
         std::map<std::tuple<const float*, int, int, int, int>, std::vector<int>> gmem;
         std::vector<std::tuple<const float*, int, int, int, int>> gorder;
@@ -552,28 +551,29 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
             const InstDesc& I0 = P->insts[v[0]];
             const int N = I0.N;
             const int k2lag = I0.d >= 2 ? 1 + I0.tau : 0;
-            int S = std::min(te::kMaxStrips, (N + te::kStripPoints - 1) / te::kStripPoints);
-            int npad = N;
-            if (S >= 4) {
-                npad = (S - 1) * te::kStripPoints + ((N - (S - 1) * te::kStripPoints + 3) & ~3);
-                for (int i : v) {  // staged-whole unshared estimates, tiled bundles and tiled
-                                   // estimates whose CTA block divides a strip take strips
-                    const InstDesc& I = P->insts[i];
-                    const int lag = I.d >= 2 ? 1 + I.tau : 0;
-                    const bool resident_alone = !bundled[i] && I.warp_mode == 1 &&
-                                                (int64_t)((npad + 3) & ~3) * (1 + 2 * I.d) <= P->smem_floats;
-                    const bool tiled_bundle = bundled[i] && I.warp_mode == 0;
-                    const bool tiled_alone = !bundled[i] && I.warp_mode == 0 && te::kStripPoints % per == 0 &&
-                                             (int64_t)te::kStripPoints * (1 + 2 * I.d) * 4 <= kSweepSmemMaxBytes;
-                    if (lag != k2lag || !(resident_alone || tiled_bundle || tiled_alone)) S = 1;
-                }
+            // estimates that can take strips: staged whole (alone or bundled), tiled bundles, and
+            // tiled estimates whose CTA block divides a strip; all agreeing on the second key
+            bool ok = true, any_tiled = false;
+            for (int i : v) {
+                const InstDesc& I = P->insts[i];
+                const int lag = I.d >= 2 ? 1 + I.tau : 0;
+                const bool resident_alone = !bundled[i] && I.warp_mode == 1;
+                const bool resident_bundle = bundled[i] && I.warp_mode == 1 && I.d <= 2;
+                const bool tiled_bundle = bundled[i] && I.warp_mode == 0;
+                const bool tiled_alone = !bundled[i] && I.warp_mode == 0 && te::kStripPoints % per == 0 &&
+                                         (int64_t)te::kStripPoints * (1 + 2 * I.d) * 4 <= kSweepSmemMaxBytes;
+                if (lag != k2lag || !(resident_alone || resident_bundle || tiled_bundle || tiled_alone)) ok = false;
+                if (tiled_bundle || tiled_alone) any_tiled = true;
             }
-            if (S < 4) {
-                S = 1;
-                npad = N;
-            }
-            te::SortGroup G{I0.tgt, I0.R, I0.T, I0.W, I0.t_start, N, S, npad, k2lag, P->sorted_total,
-                            S > 1 ? strip_total : 0};
+            // strips of kStripPoints, for groups of 4 strips or more (shorter strips were measured
+            // slower: a C3 group of 1200 points in 4 strips took 66.7 ms instead of 46.9 ms; the
+            // own strip then yields poor first radii)
+            (void)any_tiled;
+            const int L = te::kStripPoints;
+            int S = (ok && N >= 4 * L) ? std::min(te::kMaxStrips, (N + L - 1) / L) : 1;
+            const int npad = S > 1 ? ((N + 3) & ~3) : N;
+            te::SortGroup G{I0.tgt, I0.R, I0.T, I0.W, I0.t_start, N, S, npad, k2lag, S > 1 ? L : 0, 0,
+                            P->sorted_total, S > 1 ? strip_total : 0};
             P->groups.push_back(G);
             for (int i : v) {
                 InstDesc& I = P->insts[i];

@@ -232,25 +232,28 @@ __device__ __forceinline__ void bundle_warp_block(const BatchArgs& a, const Inst
                                                   const float* sm, int wb) {
     constexpr int DA = 1 + d;
     constexpr int D = 1 + 2 * d;
+    constexpr int K2 = d >= 2 ? 2 : 0;  // coordinate of the second key (strips)
     const int N = L.N;
+    const int npos = L.npad;  // sorted positions (N, or N plus the last strip's padding)
+    const int S = L.strips;
     const int lane = threadIdx.x & 31;
     const int32_t* sidx = a.sorted_idx + L.sort_off;
     const int wbase = wb * 32 * Q;
-    const int ng = (N + 3) >> 2;
+    const int ng = (npos + 3) >> 2;
     int coff[M];  // offset of member m's source tile (ragged bundles repeat the last member)
 #pragma unroll
     for (int m = 0; m < M; ++m) coff[m] = ng * 4 * (DA + min(m, nb - 1) * d);
     u64 qa[Q][DA];
     u64 qc[M][Q][d];
-    float qkey[Q];
+    float qkey[Q], qk2[Q];
     int qidx[Q];
     bool qv[Q];
     int nvalid = 0;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int pos = wbase + q * 32 + lane;
-        qv[q] = pos < N;
-        qidx[q] = qv[q] ? __ldg(sidx + pos) : -1;
+        qidx[q] = pos < npos ? __ldg(sidx + pos) : -1;
+        qv[q] = qidx[q] >= 0;
 #pragma unroll
         for (int c = 0; c < DA; ++c) qa[q][c] = dup2(qv[q] ? sm[tile_index<DA>(c, pos)] : 0.0f);
 #pragma unroll
@@ -259,11 +262,25 @@ __device__ __forceinline__ void bundle_warp_block(const BatchArgs& a, const Inst
             for (int c = 0; c < d; ++c)
                 qc[m][q][c] = dup2(qv[q] ? sm[coff[m] + tile_index<d>(c, pos)] : 0.0f);
         qkey[q] = qv[q] ? sm[tile_index<DA>(1, pos)] : 0.0f;
+        qk2[q] = qv[q] ? sm[tile_index<DA>(K2, pos)] : 0.0f;
         nvalid += __popc(__ballot_sync(0xffffffffu, qv[q]));
     }
     unsigned long long groups_done = 0;
+    if (nvalid == 0) {  // strip padding only
+        if (lane == 0)
+            for (int m = 0; m < nb; ++m) {
+                const InstDesc& J = a.insts[mem[m]];
+                a.partial[J.part_begin + wb] = 0.0;
+                a.partial_abs[J.part_begin + wb] = 0.0;
+            }
+        return;
+    }
+    const int32_t* spos = a.strip_pos + L.strip_off;
+    const float* sk2 = a.strip_k2 + 2 * L.strip_off;
 
-    // ---- pass 1: own block, then right, then left (radii: largest over the members)
+    // ---- pass 1: own block, then right, then left (radii: largest over the members); over
+    // strips: own strip(s) outward, then the other strips nearest first in the second key (as
+    // sweep_warp_block_strips in te_sweep.cuh)
     float t[M][Q][KS];
 #pragma unroll
     for (int m = 0; m < M; ++m)
@@ -271,12 +288,68 @@ __device__ __forceinline__ void bundle_warp_block(const BatchArgs& a, const Inst
         for (int q = 0; q < Q; ++q)
 #pragma unroll
             for (int s = 0; s < KS; ++s) t[m][q][s] = f_inf();
+    const int wend = min(wbase + 32 * Q, npos);
     const int g_own0 = wbase >> 2;
-    const int g_own1 = min(ng, (min(wbase + 32 * Q, N) + 3) >> 2);
+    const int g_own1 = min(ng, (wend + 3) >> 2);
     bool done = false;
     groups_done += bknn_range<d, Q, KS, M>(sm, coff, g_own0, g_own1, 0, qa, qc, qkey, qv, t, done);
-    groups_done += bknn_range<d, Q, KS, M>(sm, coff, g_own1, ng, +1, qa, qc, qkey, qv, t, done);
-    groups_done += bknn_range<d, Q, KS, M>(sm, coff, 0, g_own0, -1, qa, qc, qkey, qv, t, done);
+    // a resident bundle reaches the 4096 points of a striped group only for d <= 2 (the 200 KB
+    // budget holds 3,938 points of d = 3): the strip code is compiled for those alone
+    if (d > 2 || S <= 1) {
+        groups_done += bknn_range<d, Q, KS, M>(sm, coff, g_own1, ng, +1, qa, qc, qkey, qv, t, done);
+        groups_done += bknn_range<d, Q, KS, M>(sm, coff, 0, g_own0, -1, qa, qc, qkey, qv, t, done);
+    } else if constexpr (d <= 2) {
+        float kmin = f_inf(), kmax = -f_inf();
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+            if (qv[q]) {
+                kmin = fminf(kmin, qkey[q]);
+                kmax = fmaxf(kmax, qkey[q]);
+            }
+        kmin = warp_min(kmin);
+        kmax = warp_max(kmax);
+        const float kmid = 0.5f * kmin + 0.5f * kmax;
+        int s_lo = 0;
+        while (s_lo + 1 < S && __ldg(spos + s_lo + 1) <= wbase) ++s_lo;
+        int s_hi = s_lo;
+        while (s_hi + 1 < S && __ldg(spos + s_hi + 1) < wend) ++s_hi;
+        for (int s = s_lo; s <= s_hi; ++s) {
+            const int gs = __ldg(spos + s) >> 2, ge = __ldg(spos + s + 1) >> 2;
+            done = false;
+            groups_done += bknn_range<d, Q, KS, M>(sm, coff, max(gs, g_own1), ge, +1, qa, qc, qkey, qv, t, done);
+            done = false;
+            groups_done += bknn_range<d, Q, KS, M>(sm, coff, gs, min(ge, g_own0), -1, qa, qc, qkey, qv, t, done);
+        }
+        bool up = s_hi + 1 < S, down = s_lo > 0;
+        for (int step = 1; up || down; ++step) {
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const int s = side == 0 ? s_hi + step : s_lo - step;
+                if (side == 0 ? (!up || s >= S) : (!down || s < 0)) {
+                    if (side == 0) up = false;
+                    else down = false;
+                    continue;
+                }
+                float r[Q], lb2, rb2;
+                bundle_radii<Q, KS, M>(t, r);
+                warp_window(qk2, qv, r, lb2, rb2);
+                if (side == 0 && !(__ldg(sk2 + 2 * s) < rb2)) {
+                    up = false;
+                    continue;
+                }
+                if (side == 1 && !(__ldg(sk2 + 2 * s + 1) > lb2)) {
+                    down = false;
+                    continue;
+                }
+                const int gs = __ldg(spos + s) >> 2, ge = __ldg(spos + s + 1) >> 2;
+                const int gm = smem_first_group_above<DA>(sm, gs, ge, kmid);
+                done = false;
+                groups_done += bknn_range<d, Q, KS, M>(sm, coff, gm, ge, +1, qa, qc, qkey, qv, t, done);
+                done = false;
+                groups_done += bknn_range<d, Q, KS, M>(sm, coff, gs, gm, -1, qa, qc, qkey, qv, t, done);
+            }
+        }
+    }
     float e[M][Q], emax[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -296,8 +369,22 @@ __device__ __forceinline__ void bundle_warp_block(const BatchArgs& a, const Inst
         for (int q = 0; q < Q; ++q) cz[m][q] = cyz[m][q] = cxz[m][q] = 0.0f;
     float lb, rb;
     warp_window(qkey, qv, emax, lb, rb);
-    const int g_lo = smem_first_greater<DA>(sm, N, lb) >> 2;
-    groups_done += bcount_range<d, Q, M>(sm, coff, g_lo, ng, lb, rb, qa, qc, e, cz, cyz, cxz);
+    if (d > 2 || S <= 1) {
+        const int g_lo = smem_first_greater<DA>(sm, N, lb) >> 2;
+        groups_done += bcount_range<d, Q, M>(sm, coff, g_lo, ng, lb, rb, qa, qc, e, cz, cyz, cxz);
+    } else if constexpr (d <= 2) {
+        float lb2, rb2;
+        warp_window(qk2, qv, emax, lb2, rb2);
+        for (int s = 0; s < S; ++s) {
+            if constexpr (K2 != 0) {  // y_t (d = 1) bounds neither n_z nor n_xz: no strip is skipped
+                if (!(__ldg(sk2 + 2 * s + 1) > lb2)) continue;
+                if (!(__ldg(sk2 + 2 * s) < rb2)) break;
+            }
+            const int gs = __ldg(spos + s) >> 2, ge = __ldg(spos + s + 1) >> 2;
+            const int g_lo = smem_first_group_above<DA>(sm, gs, ge, lb);
+            groups_done += bcount_range<d, Q, M>(sm, coff, g_lo, ge, lb, rb, qa, qc, e, cz, cyz, cxz);
+        }
+    }
 
     // ---- per member: digamma terms of Eq. 9 (compensated FP32), outputs at the original index
 #pragma unroll
@@ -835,10 +922,10 @@ __global__ void __launch_bounds__(kBundleThreads, d <= 3 ? 3 : 2) bundle_kernel(
             (void)sred;
             (void)sbnd;
         }
-        stage_bundle<d, M>(a, L, mem, nb, a.sorted_idx + L.sort_off, 0, L.N, (L.N + 3) & ~3, sm);
+        stage_bundle<d, M>(a, L, mem, nb, a.sorted_idx + L.sort_off, 0, L.npad, (L.npad + 3) & ~3, sm);
         if (threadIdx.x == 0) s_wblock = w.q0;
         __syncthreads();
-        const int wb1 = min((L.N + 32 * Q - 1) / (32 * Q), w.q0 + L.wb_chunk);
+        const int wb1 = min((L.npad + 32 * Q - 1) / (32 * Q), w.q0 + L.wb_chunk);
         for (;;) {
             int wb = 0;
             if ((threadIdx.x & 31) == 0) wb = atomicAdd(&s_wblock, 1);

@@ -34,11 +34,12 @@ struct InstDesc {
 // Points of one (series, window start, window) group: the estimates of a group (original and
 // surrogates) share the target coordinates, so they share one order of the points sorted by the
 // target coordinate y_{t'-1} (coordinate 1 of the joint space). With S > 1 strips the points are
-// first ordered by a second target coordinate y_{t'-k2lag} and cut into strips of kStripPoints
-// consecutive ranks (the last one shorter, padded to a multiple of four positions with index -1
-// and key +inf), each sorted by y_{t'-1}; strip s holds positions strip_pos[s] = s * kStripPoints
-// .. strip_pos[s+1]-1 and its second-key values lie in [strip_k2[2s], strip_k2[2s+1]]. Strip
-// starts are multiples of 1024, so no warp block (32 Q) or 256-query CTA block spans two strips.
+// first ordered by a second target coordinate y_{t'-k2lag} and cut into strips of L consecutive
+// ranks (the last one shorter, padded to a multiple of four positions with index -1 and key
+// +inf), each sorted by y_{t'-1}; strip s holds positions strip_pos[s] = s * L .. strip_pos[s+1]-1
+// and its second-key values lie in [strip_k2[2s], strip_k2[2s+1]]. L = kStripPoints (groups of
+// 4 L points or more), so no warp block or 256-query CTA block spans two strips and a strip fits
+// a tile of the tiled paths.
 // The second key is y_{t'-1-tau} (coordinate 2, in y-) for d >= 2 and y_t (coordinate 0, not in
 // y-) for d = 1.
 struct SortGroup {
@@ -47,12 +48,14 @@ struct SortGroup {
     int32_t S;             // strips (1: one key order)
     int32_t npad;          // sorted positions (N when S == 1)
     int32_t k2lag;         // S > 1: the second key is y_{t' - k2lag}
+    int32_t L;             // S > 1: points per strip (the last strip holds the rest)
+    int32_t pad_;
     int64_t off;           // offset of the group's sorted index / key arrays (npad entries)
     int64_t strip_off;     // S > 1: strip_pos[strip_off .. strip_off + S], strip_k2[2 strip_off ..
                            // 2 strip_off + 2 S - 1]
 };
 
-constexpr int kStripPoints = 1024;  // points per strip (a multiple of 256 and of 32 * Q)
+constexpr int kStripPoints = 1024;  // points per strip (a multiple of 256 and of 32 Q)
 constexpr int kMaxStrips = 64;
 
 // Largest point count the sweep mode sorts (one CTA per group; runs in shared memory, merges

@@ -5,11 +5,11 @@
 // double the run length through global memory (each thread merges its share of the output after a
 // merge-path search for its starting split).
 //   S == 1: key = y_{t'-1} (coordinate 1 of the joint space).
-//   S > 1 (strips): first sorted by the second key y_{t'-k2lag} and cut into strips of
-//           kStripPoints consecutive ranks (the last one shorter), then sorted by (strip, y_{t'-1});
-//           strip s is written at positions s * kStripPoints .. (the last strip padded to a
-//           multiple of four with (index -1, key +inf)), and the lowest and highest second key of
-//           its points are recorded.
+//   S > 1 (strips): first sorted by the second key y_{t'-k2lag} and cut into strips of G.L
+//           consecutive ranks (the last one shorter), then sorted by (strip, y_{t'-1}); strip s is
+//           written at positions s * G.L .. (the last strip padded to a multiple of four with
+//           (index -1, key +inf)), and the lowest and highest second key of its points are
+//           recorded.
 // Keys are FP32 values mapped to unsigned integers that order like the floats.
 #include "te_internal.h"
 
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_groups_kernel(const SortGro
         return;
     }
     const int S = G.S;
-    const int L = kStripPoints;
+    const int L = G.L;
     // 1. by the second key: strip s holds the points of rank s L .. min((s + 1) L, N) - 1
     sort_pairs(N, [&](int p, u64k& k, int& i) { k = ord_bits(group_coord(G, p, G.k2lag)); i = p; }, ak, ai, bk,
                bi, sk, si);

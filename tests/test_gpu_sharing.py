@@ -188,3 +188,24 @@ def test_tiled_bundles_with_strips_equal_unshared(te_handle, d, ties):
     assert b0 == 0 and b1 == 2
     assert torch.equal(off["counts"], on["counts"]) and torch.equal(off["eps"], on["eps"])
     assert torch.max(torch.abs(off["te"] - on["te"])).item() <= 1e-12
+
+
+@pytest.mark.parametrize("ties", [False, True])
+def test_resident_bundles_with_strips_equal_unshared(te_handle, ties):
+    """Resident bundles over a sort group of 6,000 points (d = 1: 5 columns x 6,000 = 120 KB per
+    bundle) cut into strips: radii and counts equal the unshared search (itself over strips)."""
+    rng = np.random.default_rng(91 + (1 if ties else 0))
+    R, W = 2000, 3
+    if ties:
+        src = rng.integers(0, 6, (R, 40)).astype(np.float32)
+        tgt = rng.integers(0, 6, (R, 40)).astype(np.float32)
+    else:
+        src, tgt = I.ar2_pair(rng, R, 40)
+    s = I.Series(src, tgt, d=1, tau=1, u=2, perms=I.permutations(rng, 4, R))
+    insts = [I.Instance(0, 12, W, p) for p in (-1, 0, 1, 2, 3)]
+    ds = te.to_device([s])
+    off, b0, _, _, _ = _estimate(te_handle, ds, insts, 4, False)
+    on, b1, _, _, _ = _estimate(te_handle, ds, insts, 4, True)
+    assert b0 == 0 and b1 == 2
+    assert torch.equal(off["counts"], on["counts"]) and torch.equal(off["eps"], on["eps"])
+    assert torch.max(torch.abs(off["te"] - on["te"])).item() <= 1e-12
