@@ -337,7 +337,6 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
                      int n_inst, int k, Plan* P) {
     P->insts.resize(n_inst);
     int dlo = 99, dhi = 0, nmax = 0, dmaxN = 0;
-    int dmaxN_strips = 0;  // dmaxN with the padding of the strips a group of this size may get
     int64_t off = 0;
     for (int i = 0; i < n_inst; ++i) {
         const te_instance& in = inst[i];
@@ -371,7 +370,6 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
         dhi = std::max(dhi, S.d);
         nmax = std::max(nmax, (int)N);
         dmaxN = std::max(dmaxN, (int)(((N + 3) & ~3) * (1 + 2 * S.d)));
-        dmaxN_strips = std::max(dmaxN_strips, (int)(((N + 3) & ~3) * (1 + 2 * S.d)));
     }
     P->n_points = off;
     if (dlo != dhi && dhi > kMaxMixedD)
@@ -404,7 +402,7 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
         // every instance resident in shared memory (up to kResidentMaxBytes) when it fits there,
         // which lets warps balance the work; otherwise tiles of whole CTA query blocks
         if (!h->per_instance && (int64_t)dmaxN * (int64_t)sizeof(float) <= kResidentMaxBytes) {
-            P->smem_floats = std::max(P->smem_floats, std::min(dmaxN_strips, (int)(kResidentMaxBytes / 4)));
+            P->smem_floats = std::max(P->smem_floats, dmaxN);
         } else {
             int need = P->smem_floats;
             for (const auto& I : P->insts) {
@@ -553,7 +551,7 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
             const int k2lag = I0.d >= 2 ? 1 + I0.tau : 0;
             // estimates that can take strips: staged whole (alone or bundled), tiled bundles, and
             // tiled estimates whose CTA block divides a strip; all agreeing on the second key
-            bool ok = true, any_tiled = false;
+            bool ok = true;
             for (int i : v) {
                 const InstDesc& I = P->insts[i];
                 const int lag = I.d >= 2 ? 1 + I.tau : 0;
@@ -563,12 +561,10 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
                 const bool tiled_alone = !bundled[i] && I.warp_mode == 0 && te::kStripPoints % per == 0 &&
                                          (int64_t)te::kStripPoints * (1 + 2 * I.d) * 4 <= kSweepSmemMaxBytes;
                 if (lag != k2lag || !(resident_alone || resident_bundle || tiled_bundle || tiled_alone)) ok = false;
-                if (tiled_bundle || tiled_alone) any_tiled = true;
             }
             // strips of kStripPoints, for groups of 4 strips or more (shorter strips were measured
             // slower: a C3 group of 1200 points in 4 strips took 66.7 ms instead of 46.9 ms; the
             // own strip then yields poor first radii)
-            (void)any_tiled;
             const int L = te::kStripPoints;
             int S = (ok && N >= 4 * L) ? std::min(te::kMaxStrips, (N + L - 1) / L) : 1;
             const int npad = S > 1 ? ((N + 3) & ~3) : N;

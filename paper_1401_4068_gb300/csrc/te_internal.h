@@ -49,7 +49,7 @@ struct SortGroup {
     int32_t npad;          // sorted positions (N when S == 1)
     int32_t k2lag;         // S > 1: the second key is y_{t' - k2lag}
     int32_t L;             // S > 1: points per strip (the last strip holds the rest)
-    int32_t pad_;
+    int32_t reserved;      // keeps the 64-bit fields aligned
     int64_t off;           // offset of the group's sorted index / key arrays (npad entries)
     int64_t strip_off;     // S > 1: strip_pos[strip_off .. strip_off + S], strip_k2[2 strip_off ..
                            // 2 strip_off + 2 S - 1]
