@@ -240,7 +240,11 @@ te_status te_last_alu_ops(te_handle* h, uint64_t* ops, int32_t* bundles);
  * launch for the whole batch, captured in a CUDA graph. per_instance = 1: the same kernel and
  * tables, launched once per instance with a grid of that instance's work items and no graph,
  * the way an unbatched implementation runs one search space per launch (the comparison of the
- * Implementation section's "several chunks per launch" design). Results are bit-identical. */
+ * Implementation section's "several chunks per launch" design). Per instance, no estimate is
+ * staged whole in shared memory and target parts are not shared, so those estimates' Eq. 9
+ * partial sums are grouped differently: counts and eps are bit-identical in both modes, TE is
+ * bit-identical where the batched launch takes the tiled path without sharing as well and
+ * otherwise agrees within the two err_bound values. */
 te_status te_set_batching(te_handle* h, int32_t per_instance);
 
 /* te_surrogate_test_static - te_surrogate_test for one series, for callers that cannot allocate

@@ -241,6 +241,25 @@ def test_per_instance_launch_mode_is_bit_identical(te_handle):
     assert torch.equal(ref["te"], got["te"])
 
 
+def test_per_instance_launch_mode_with_resident_and_shared_estimates(te_handle):
+    # C3 shapes: in one launch the estimates are staged whole and bundled by target part; per
+    # instance they run the tiled search without sharing, so the partial sums are grouped
+    # differently: counts and eps stay bit-identical, TE agrees within the error bound
+    w = I.config(3, n_t=2, S=20)
+    ds = te.to_device(w.series)
+    ref = te.te_estimate(te_handle, ds, w.instances, w.k, want_err=True, want_counts=True)
+    assert te.te_last_alu_ops(te_handle)[1] > 0
+    te.te_set_batching(te_handle, True)
+    try:
+        got = te.te_estimate(te_handle, ds, w.instances, w.k, want_err=True, want_counts=True)
+    finally:
+        te.te_set_batching(te_handle, False)
+    torch.cuda.synchronize()
+    assert torch.equal(ref["counts"], got["counts"]) and torch.equal(ref["eps"], got["eps"])
+    diff = (ref["te"] - got["te"]).abs()
+    assert bool((diff <= ref["err_bound"] + got["err_bound"]).all())
+
+
 def test_autotune_picks_a_shape_caches_it_and_keeps_results(te_handle, tmp_path):
     w = I.config(3, n_t=2, S=60)
     ds = te.to_device(w.series)
