@@ -339,6 +339,7 @@ def bench_ours(args):
     clocks = sampler.stop()
     exec_pairs, exec_ops, swept = te.te_last_work(h)
     alu_ops, bundles = te.te_last_alu_ops(h)
+    (pass_pairs, pass_cycles) = te.te_last_pass_work(h)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     if ws > 1:
@@ -351,6 +352,21 @@ def bench_ours(args):
     n_est = len(w.instances) * _scan_factor(w)
     value = ws * pe_step * args.steps / (total_ms / 1e3)
     te_rate = ws * n_est * args.steps / (total_ms / 1e3)
+
+    # ---- the two passes: the step time split by the warps' SM cycles in each pass (device clock,
+    # counted by the sweep); the algorithmic work is N (N - 1) pairs per pass
+    passes = None
+    if swept and sum(pass_cycles) > 0:
+        per_pass = pe_step / 2
+        passes = {"time_split": "step time x share of the warps' SM cycles spent in the pass (clock64 on "
+                                "the device; pass 2 includes the digamma terms)"}
+        for name, pp, cyc in (("pass1_knn", pass_pairs[0], pass_cycles[0]),
+                              ("pass2_counts", pass_pairs[1], pass_cycles[1])):
+            share = cyc / sum(pass_cycles)
+            passes[name] = {"cycle_share": round(share, 4),
+                            "pair_evals_per_s": ws * per_pass * args.steps / (total_ms * share / 1e3),
+                            "pair_evals_executed_per_step": pp,
+                            "executed_vs_algorithmic": round(pp / max(1.0, per_pass), 4)}
 
     # ---- roofline of the search kernel (CUDA events on its own stream, live): the bundle kernel
     # when target-part sharing formed bundles, else the persistent batched kernel
@@ -494,6 +510,7 @@ def bench_ours(args):
         "search": {"mode": "sorted sweep" if swept else "exhaustive",
                    "pair_evals_executed_per_step": exec_pairs,
                    "executed_vs_algorithmic": round(exec_pairs / max(1, pe_step), 4),
+                   "passes": passes,
                    "target_part_sharing": {"bundles": bundles, "alu_ops_executed_per_step": alu_ops,
                                            "alu_ops_vs_2D_per_pair": round(alu_ops / max(1, exec_ops), 4)}},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -236,6 +236,16 @@ te_status te_set_sharing(te_handle* h, int32_t enable);
  * are read from the device (synchronises the device). */
 te_status te_last_alu_ops(te_handle* h, uint64_t* ops, int32_t* bundles);
 
+/* The work of the last te_estimate / te_surrogate_test / te_delay_scan call split by pass:
+ * pairs[0], pairs[1] = (query, reference) pair evaluations of pass 1 (the k-th neighbour search,
+ * Eq. 9's eps) and of pass 2 (the three range counts), summed over estimates (pairs[0] +
+ * pairs[1] = te_last_work's pairs); cycles[0], cycles[1] = SM clock cycles the warps spent in
+ * each pass, summed over warps (pass 2 includes the digamma terms), measured on the device by
+ * the sweep: their ratio splits the kernel time between the passes. Exhaustive search: N^2
+ * pairs per pass and cycles 0 (not measured). Both arrays have two entries and must be
+ * non-NULL; synchronises the device. */
+te_status te_last_pass_work(te_handle* h, uint64_t* pairs, uint64_t* cycles);
+
 /* Batching mode of te_estimate / te_surrogate_test. per_instance = 0 (default): one persistent
  * launch for the whole batch, captured in a CUDA graph. per_instance = 1: the same kernel and
  * tables, launched once per instance with a grid of that instance's work items and no graph,

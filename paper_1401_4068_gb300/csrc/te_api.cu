@@ -733,7 +733,7 @@ te_status prepare_sweep(te_handle* h, const Plan& P, bool* grew) {
     if ((e = h->d_groups.ensure(P.groups.size(), grew)) != cudaSuccess ||
         (e = h->d_sidx.ensure((size_t)P.sorted_total, grew)) != cudaSuccess ||
         (e = h->d_skey.ensure((size_t)P.sorted_total, grew)) != cudaSuccess ||
-        (e = h->d_exec.ensure(3, grew)) != cudaSuccess ||
+        (e = h->d_exec.ensure(6, grew)) != cudaSuccess ||
         (e = h->d_bitems.ensure(P.bitems.size(), grew)) != cudaSuccess ||
         (e = h->d_members.ensure(P.members.size(), grew)) != cudaSuccess)
         return h->fail(TE_ENOMEM, "sweep workspace: %s", cudaGetErrorString(e));
@@ -751,7 +751,7 @@ te_status prepare_sweep(te_handle* h, const Plan& P, bool* grew) {
 // the sweep's pre-pass (work counters cleared, groups sorted) on `s`
 cudaError_t launch_sweep_prepass(te_handle* h, const Plan& P, cudaStream_t s) {
     if (!P.var.sweep) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(h->d_exec.p, 0, 3 * sizeof(unsigned long long), s);
+    cudaError_t e = cudaMemsetAsync(h->d_exec.p, 0, 6 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     return te::launch_sort_groups(h->d_groups.p, (int)P.groups.size(), h->d_sidx.p, h->d_skey.p, h->d_sk64a.p,
                                   h->d_sia.p, h->d_sk64b.p, h->d_sib.p, h->d_strip_pos.p, h->d_strip_k2.p, s);
@@ -1416,6 +1416,25 @@ TE_EXPORT te_status te_last_alu_ops(te_handle* h, uint64_t* ops, int32_t* bundle
     }
     *ops = op;
     if (bundles) *bundles = h->last_bundled;
+    return TE_OK;
+}
+
+TE_EXPORT te_status te_last_pass_work(te_handle* h, uint64_t* pairs, uint64_t* cycles) {
+    if (!h || !pairs || !cycles) return TE_EINVAL;
+    h->err.clear();
+    // exhaustive search: N^2 pairs per pass, no cycle accounting
+    pairs[0] = pairs[1] = h->last_pairs / 2;
+    cycles[0] = cycles[1] = 0;
+    if (h->last_sweep && h->d_exec.p) {
+        DeviceGuard g(h->device);
+        unsigned long long v[6] = {0, 0, 0, 0, 0, 0};
+        cudaError_t e = cudaMemcpy(v, h->d_exec.p, sizeof v, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return h->cuda_fail(e, "read work counters");
+        pairs[0] = v[3];
+        pairs[1] = v[0] - v[3];
+        cycles[0] = v[4];
+        cycles[1] = v[5];
+    }
     return TE_OK;
 }
 

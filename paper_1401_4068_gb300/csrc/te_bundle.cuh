@@ -230,6 +230,7 @@ __device__ __forceinline__ int bcount_range(const float* __restrict__ s, const i
 template <int d, int Q, int KS, int M>
 __device__ __forceinline__ void bundle_warp_block(const BatchArgs& a, const InstDesc& L, const int32_t* mem, int nb,
                                                   const float* sm, int wb) {
+    pass1_begin(a);
     constexpr int DA = 1 + d;
     constexpr int D = 1 + 2 * d;
     constexpr int K2 = d >= 2 ? 2 : 0;  // coordinate of the second key (strips)
@@ -273,6 +274,8 @@ __device__ __forceinline__ void bundle_warp_block(const BatchArgs& a, const Inst
                 a.partial[J.part_begin + wb] = 0.0;
                 a.partial_abs[J.part_begin + wb] = 0.0;
             }
+        pass1_end(a, 0);
+        pass2_end(a);
         return;
     }
     const int32_t* spos = a.strip_pos + L.strip_off;
@@ -360,6 +363,7 @@ __device__ __forceinline__ void bundle_warp_block(const BatchArgs& a, const Inst
             emax[q] = fmaxf(emax[q], e[m][q]);
         }
     }
+    pass1_end(a, groups_done * 4ull * (unsigned long long)nvalid * (unsigned long long)nb);
 
     // ---- pass 2: the key window of the largest eps
     float cz[M][Q], cyz[M][Q], cxz[M][Q];
@@ -429,15 +433,16 @@ __device__ __forceinline__ void bundle_warp_block(const BatchArgs& a, const Inst
             }
         }
     }
+    pass2_end(a);
     if (a.exec && lane == 0) {
         // pairs per member; 2 D algorithmic operations per pair; executed: the target part's
         // 2 (1 + d) once and 2 d per member slot (M slots, padding included)
         const unsigned long long g4 = groups_done * 4ull * (unsigned long long)nvalid;
         const unsigned long long alg = g4 * (unsigned long long)nb * 2ull * D;
         const unsigned long long run = g4 * (2ull * DA + (unsigned long long)M * 2ull * d);
-        atomicAdd(a.exec, g4 * (unsigned long long)nb);
-        atomicAdd(a.exec + 1, alg);
-        atomicAdd(a.exec + 2, alg > run ? alg - run : 0ull);
+        work_add(0, g4 * (unsigned long long)nb);
+        work_add(1, alg);
+        work_add(2, alg > run ? alg - run : 0ull);
     }
 }
 
@@ -450,6 +455,7 @@ __device__ __forceinline__ void bundle_warp_block(const BatchArgs& a, const Inst
 template <int d, int Q, int KS, int M>
 __device__ __forceinline__ void bundle_item_tiled(const BatchArgs& a, const InstDesc& L, const int32_t* mem, int nb,
                                                   int q0, int item, float* sm, double* sred, float* sbnd) {
+    pass1_begin(a);
     constexpr int DA = 1 + d;
     constexpr int D = 1 + 2 * d;
     const int N = L.N;
@@ -566,6 +572,7 @@ __device__ __forceinline__ void bundle_item_tiled(const BatchArgs& a, const Inst
             emax[q] = fmaxf(emax[q], e[m][q]);
         }
     }
+    pass1_end(a, groups_done * 4ull * (unsigned long long)nvalid * (unsigned long long)nb);
 
     // ---- pass 2: the tiles of the CTA's key window (largest eps over the members)
     float cz[M][Q], cyz[M][Q], cxz[M][Q];
@@ -634,13 +641,14 @@ __device__ __forceinline__ void bundle_item_tiled(const BatchArgs& a, const Inst
             a.partial_abs[J.part_begin + item] = w;
         }
     }
+    pass2_end(a);
     if (a.exec && warp_active && lane == 0) {
         const unsigned long long g4 = groups_done * 4ull * (unsigned long long)nvalid;
         const unsigned long long alg = g4 * (unsigned long long)nb * 2ull * D;
         const unsigned long long run = g4 * (2ull * DA + (unsigned long long)M * 2ull * d);
-        atomicAdd(a.exec, g4 * (unsigned long long)nb);
-        atomicAdd(a.exec + 1, alg);
-        atomicAdd(a.exec + 2, alg > run ? alg - run : 0ull);
+        work_add(0, g4 * (unsigned long long)nb);
+        work_add(1, alg);
+        work_add(2, alg > run ? alg - run : 0ull);
     }
 }
 
@@ -655,6 +663,7 @@ template <int d, int Q, int KS, int M>
 __device__ __forceinline__ void bundle_item_tiled_strips(const BatchArgs& a, const InstDesc& L, const int32_t* mem,
                                                          int nb, int q0, int item, float* sm, double* sred,
                                                          float* sbnd) {
+    pass1_begin(a);
     constexpr int DA = 1 + d;
     constexpr int D = 1 + 2 * d;
     constexpr int K2 = d >= 2 ? 2 : 0;
@@ -801,6 +810,7 @@ __device__ __forceinline__ void bundle_item_tiled_strips(const BatchArgs& a, con
             emax[q] = fmaxf(emax[q], e[m][q]);
         }
     }
+    pass1_end(a, groups_done * 4ull * (unsigned long long)nvalid * (unsigned long long)nb);
 
     // ---- pass 2
     float cz[M][Q], cyz[M][Q], cxz[M][Q];
@@ -879,13 +889,14 @@ __device__ __forceinline__ void bundle_item_tiled_strips(const BatchArgs& a, con
             a.partial_abs[J.part_begin + item] = w;
         }
     }
+    pass2_end(a);
     if (a.exec && warp_active && lane == 0) {
         const unsigned long long g4 = groups_done * 4ull * (unsigned long long)nvalid;
         const unsigned long long alg = g4 * (unsigned long long)nb * 2ull * D;
         const unsigned long long run = g4 * (2ull * DA + (unsigned long long)M * 2ull * d);
-        atomicAdd(a.exec, g4 * (unsigned long long)nb);
-        atomicAdd(a.exec + 1, alg);
-        atomicAdd(a.exec + 2, alg > run ? alg - run : 0ull);
+        work_add(0, g4 * (unsigned long long)nb);
+        work_add(1, alg);
+        work_add(2, alg > run ? alg - run : 0ull);
     }
 }
 
@@ -901,6 +912,7 @@ __global__ void __launch_bounds__(kBundleThreads, d <= 3 ? 3 : 2) bundle_kernel(
     __shared__ float sbnd[64];
     __shared__ int s_item;
     __shared__ int s_wblock;
+    work_reset();
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
@@ -934,6 +946,7 @@ __global__ void __launch_bounds__(kBundleThreads, d <= 3 ? 3 : 2) bundle_kernel(
             bundle_warp_block<d, Q, KS, M>(a, L, mem, nb, sm, wb);
         }
     }
+    work_flush(a);
 }
 
 }  // namespace te

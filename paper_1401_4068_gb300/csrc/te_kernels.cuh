@@ -15,6 +15,7 @@ __global__ void __launch_bounds__(kBatchedMaxThreads) batched_kernel(const Batch
     __shared__ float sbnd[64];
     __shared__ int s_item;
     __shared__ int s_wblock;
+    if constexpr (SWEEP) work_reset();
     for (;;) {
         __syncthreads();  // everyone is done with s_item / sred of the previous item
         if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
@@ -52,6 +53,7 @@ __global__ void __launch_bounds__(kBatchedMaxThreads) batched_kernel(const Batch
         }
 #undef TE_PROCESS
     }
+    if constexpr (SWEEP) work_flush(a);
 }
 
 // Sweep kernel for batches whose every estimate is staged whole in shared memory (warp mode)
@@ -62,6 +64,7 @@ __global__ void __launch_bounds__(kSweepWarpThreads) sweep_warp_kernel(const Bat
     extern __shared__ __align__(16) float sm[];
     __shared__ int s_item;
     __shared__ int s_wblock;
+    work_reset();
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
@@ -72,6 +75,7 @@ __global__ void __launch_bounds__(kSweepWarpThreads) sweep_warp_kernel(const Bat
         const InstDesc I = a.insts[w.inst];
         process_instance_sweep_warps<DD, Q, KS>(a, I, w.q0, sm, &s_wblock);
     }
+    work_flush(a);
 }
 
 #define TE_SWEEP_WARP_PTR_FN(NAME, DD)                                                           \

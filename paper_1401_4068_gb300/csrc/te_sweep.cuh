@@ -31,6 +31,46 @@ __device__ __forceinline__ float warp_max(float v) {
 }
 
 // CTA-wide min of a and max of b (every thread gets both); sb: 64 floats of shared memory
+// Work counters of the sweep, per warp in shared memory (lane 0 only): [0] (query, reference)
+// pair evaluations, [1] their 2 D FP32 operations, [2] operations target-part sharing saved,
+// [3] pass-1 pair evaluations, [4] the warp's cycles in pass 1, [5] its cycles in pass 2 (digamma
+// terms included). A pass's cycles are added as -clock64() at its start and clock64() at its end
+// (sums exact modulo 2^64, so no register stays live across a pass). The persistent kernels add
+// the slots to BatchArgs::exec once, when the CTA leaves its work loop, so a warp block costs no
+// global atomics.
+__device__ __forceinline__ unsigned long long* work_slot() {
+    __shared__ unsigned long long s_work[32][6];
+    return s_work[threadIdx.x >> 5];
+}
+__device__ __forceinline__ void work_add(int i, unsigned long long v) { work_slot()[i] += v; }
+__device__ __forceinline__ void work_reset() {
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) work_slot()[i] = 0;
+}
+__device__ __forceinline__ void work_flush(const BatchArgs& a) {
+    if (a.exec && (threadIdx.x & 31) == 0) {
+        const unsigned long long* w = work_slot();
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+            if (w[i]) atomicAdd(a.exec + i, w[i]);
+    }
+}
+__device__ __forceinline__ void pass1_begin(const BatchArgs& a) {
+    if (a.exec && (threadIdx.x & 31) == 0) work_add(4, 0ull - (unsigned long long)clock64());
+}
+__device__ __forceinline__ void pass1_end(const BatchArgs& a, unsigned long long pairs1) {
+    if (a.exec && (threadIdx.x & 31) == 0) {
+        const unsigned long long c = (unsigned long long)clock64();
+        work_add(4, c);
+        work_add(5, 0ull - c);
+        work_add(3, pairs1);
+    }
+}
+__device__ __forceinline__ void pass2_end(const BatchArgs& a) {
+    if (a.exec && (threadIdx.x & 31) == 0) work_add(5, (unsigned long long)clock64());
+}
+
 __device__ __forceinline__ void block_minmax(float& a, float& b, float* sb) {
     a = warp_min(a);
     b = warp_max(b);
@@ -183,6 +223,7 @@ __device__ __forceinline__ int first_not_less(const float* __restrict__ key, int
 template <int d, int Q, int KS>
 __device__ __forceinline__ void process_item_sweep(const BatchArgs& a, const InstDesc& I, int q0, int it, float* sm,
                                                    double* sred, float* sb) {
+    pass1_begin(a);
     constexpr int D = 1 + 2 * d;
     const int N = I.N;
     const int T = blockDim.x;
@@ -277,6 +318,7 @@ __device__ __forceinline__ void process_item_sweep(const BatchArgs& a, const Ins
     float e[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) e[q] = topk_select(t[q], a.k);
+    pass1_end(a, groups_done * 4ull * (unsigned long long)nvalid);
 
     // ---- pass 2: only the key window (key_q - eps, key_q + eps) of the CTA's queries
     float cz[Q], cyz[Q], cxz[Q];
@@ -321,10 +363,11 @@ __device__ __forceinline__ void process_item_sweep(const BatchArgs& a, const Ins
             acc_abs += fabsf(p1.x) + fabsf(p2.x) + fabsf(p3.x);
         }
     }
+    pass2_end(a);
     if (a.exec && warp_active && lane == 0) {
         const unsigned long long pairs = groups_done * 4ull * (unsigned long long)nvalid;
-        atomicAdd(a.exec, pairs);
-        atomicAdd(a.exec + 1, pairs * 2ull * D);
+        work_add(0, pairs);
+        work_add(1, pairs * 2ull * D);
     }
     double v = (double)acc.hi + (double)acc.lo;
     double w = (double)acc_abs;
@@ -353,6 +396,7 @@ __device__ __forceinline__ int smem_first_greater(const float* __restrict__ s, i
 template <int d, int Q, int KS>
 __device__ __forceinline__ void sweep_warp_block(const BatchArgs& a, const InstDesc& I, const float* sm, int wb,
                                                  int part) {
+    pass1_begin(a);
     constexpr int D = 1 + 2 * d;
     const int N = I.N;
     const int lane = threadIdx.x & 31;
@@ -390,6 +434,7 @@ __device__ __forceinline__ void sweep_warp_block(const BatchArgs& a, const InstD
     float e[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) e[q] = topk_select(t[q], a.k);
+    pass1_end(a, groups_done * 4ull * (unsigned long long)nvalid);
 
     float cz[Q], cyz[Q], cxz[Q];
 #pragma unroll
@@ -430,13 +475,14 @@ __device__ __forceinline__ void sweep_warp_block(const BatchArgs& a, const InstD
         v += __shfl_down_sync(0xffffffffu, v, o);
         w += __shfl_down_sync(0xffffffffu, w, o);
     }
+    pass2_end(a);
     if (lane == 0) {
         a.partial[part] = v;
         a.partial_abs[part] = w;
         if (a.exec) {
             const unsigned long long pairs = groups_done * 4ull * (unsigned long long)nvalid;
-            atomicAdd(a.exec, pairs);
-            atomicAdd(a.exec + 1, pairs * 2ull * D);
+            work_add(0, pairs);
+            work_add(1, pairs * 2ull * D);
         }
     }
 }
@@ -451,6 +497,7 @@ __device__ __forceinline__ void sweep_warp_block(const BatchArgs& a, const InstD
 template <int d, int Q, int KS>
 __device__ __forceinline__ void process_item_sweep_strips(const BatchArgs& a, const InstDesc& I, int q0, int it,
                                                           float* sm, double* sred, float* sbnd) {
+    pass1_begin(a);
     constexpr int D = 1 + 2 * d;
     constexpr int K2 = d >= 2 ? 2 : 0;
     const int N = I.N;
@@ -561,6 +608,7 @@ __device__ __forceinline__ void process_item_sweep_strips(const BatchArgs& a, co
     float e[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) e[q] = topk_select(t[q], a.k);
+    pass1_end(a, groups_done * 4ull * (unsigned long long)nvalid);
 
     float cz[Q], cyz[Q], cxz[Q];
 #pragma unroll
@@ -613,10 +661,11 @@ __device__ __forceinline__ void process_item_sweep_strips(const BatchArgs& a, co
             acc_abs += fabsf(p1.x) + fabsf(p2.x) + fabsf(p3.x);
         }
     }
+    pass2_end(a);
     if (a.exec && warp_active && lane == 0) {
         const unsigned long long pairs = groups_done * 4ull * (unsigned long long)nvalid;
-        atomicAdd(a.exec, pairs);
-        atomicAdd(a.exec + 1, pairs * 2ull * D);
+        work_add(0, pairs);
+        work_add(1, pairs * 2ull * D);
     }
     double v = (double)acc.hi + (double)acc.lo;
     double w = (double)acc_abs;
@@ -652,6 +701,7 @@ __device__ __forceinline__ int smem_first_group_above(const float* __restrict__ 
 template <int d, int Q, int KS>
 __device__ __forceinline__ void sweep_warp_block_strips(const BatchArgs& a, const InstDesc& I, const float* sm,
                                                         int wb, int part) {
+    pass1_begin(a);
     constexpr int D = 1 + 2 * d;
     constexpr int K2 = d >= 2 ? 2 : 0;  // coordinate of the second key
     const int N = I.N;
@@ -684,6 +734,8 @@ __device__ __forceinline__ void sweep_warp_block_strips(const BatchArgs& a, cons
             a.partial[part] = 0.0;
             a.partial_abs[part] = 0.0;
         }
+        pass1_end(a, 0);
+        pass2_end(a);
         return;
     }
     // median-ish entry key: the middle valid query key of the warp
@@ -753,6 +805,7 @@ __device__ __forceinline__ void sweep_warp_block_strips(const BatchArgs& a, cons
     float e[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) e[q] = topk_select(t[q], a.k);
+    pass1_end(a, groups_done * 4ull * (unsigned long long)nvalid);
 
     // ---- pass 2: the key1 window of every strip (d >= 2: whose key2 range meets the window; the
     // counts of n_z and n_xz do not involve y_t, so for d = 1 no strip is skipped)
@@ -803,13 +856,14 @@ __device__ __forceinline__ void sweep_warp_block_strips(const BatchArgs& a, cons
         v += __shfl_down_sync(0xffffffffu, v, o);
         w += __shfl_down_sync(0xffffffffu, w, o);
     }
+    pass2_end(a);
     if (lane == 0) {
         a.partial[part] = v;
         a.partial_abs[part] = w;
         if (a.exec) {
             const unsigned long long pairs = groups_done * 4ull * (unsigned long long)nvalid;
-            atomicAdd(a.exec, pairs);
-            atomicAdd(a.exec + 1, pairs * 2ull * D);
+            work_add(0, pairs);
+            work_add(1, pairs * 2ull * D);
         }
     }
 }

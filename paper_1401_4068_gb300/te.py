@@ -29,7 +29,7 @@ EXPORTS = ["te_create", "te_destroy", "te_last_error", "te_sync_status", "te_emb
            "te_knn_maxnorm", "te_range_count", "te_estimate", "te_surrogate_test",
            "te_set_profiling", "te_last_kernel_ms", "te_last_launch_count", "te_set_launch_config",
            "te_set_batching", "te_surrogate_test_static", "te_autotune", "te_delay_scan",
-           "te_set_search", "te_last_work", "te_set_sharing", "te_last_alu_ops"]
+           "te_set_search", "te_last_work", "te_set_sharing", "te_last_alu_ops", "te_last_pass_work"]
 
 
 class TEError(RuntimeError):
@@ -94,13 +94,14 @@ def load() -> C.CDLL:
     lib.te_last_work.argtypes = [P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(i32)]
     lib.te_set_sharing.argtypes = [P, i32]
     lib.te_last_alu_ops.argtypes = [P, C.POINTER(C.c_uint64), C.POINTER(i32)]
+    lib.te_last_pass_work.argtypes = [P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
     lib.te_delay_scan.argtypes = [P, C.POINTER(te_series), P, i32, i32, i32, i32, i32, i32, P, P, P, P]
     lib.te_autotune.argtypes = [P, C.POINTER(te_series), i32, C.POINTER(te_instance), i32, i32,
                                 C.c_char_p, C.POINTER(i32), C.POINTER(i32), P]
     for name in ("te_sync_status", "te_embed", "te_knn_maxnorm", "te_range_count", "te_estimate",
                  "te_surrogate_test", "te_set_profiling", "te_last_kernel_ms",
                  "te_last_launch_count", "te_set_launch_config", "te_set_batching", "te_autotune", "te_delay_scan",
-                 "te_set_search", "te_last_work", "te_set_sharing", "te_last_alu_ops"):
+                 "te_set_search", "te_last_work", "te_set_sharing", "te_last_alu_ops", "te_last_pass_work"):
         getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -369,6 +370,14 @@ def te_last_work(h: Handle):
 def te_set_sharing(h: Handle, enable: bool):
     """True (default): estimates with one target part run in bundles that compute it once."""
     h.check(h.lib.te_set_sharing(h.h, 1 if enable else 0))
+
+
+def te_last_pass_work(h: Handle):
+    """((pass-1 pairs, pass-2 pairs), (pass-1 warp cycles, pass-2 warp cycles)) of the last
+    batched call; cycles are 0 for the exhaustive search."""
+    pr, cy = (C.c_uint64 * 2)(), (C.c_uint64 * 2)()
+    h.check(h.lib.te_last_pass_work(h.h, pr, cy))
+    return (int(pr[0]), int(pr[1])), (int(cy[0]), int(cy[1]))
 
 
 def te_last_alu_ops(h: Handle):

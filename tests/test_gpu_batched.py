@@ -309,15 +309,22 @@ def test_sorted_sweep_equals_exhaustive_search(te_handle, case):
     try:
         ref = te.te_estimate(te_handle, ds, w.instances, w.k, want_counts=True)
         ex_pairs, _, swept0 = te.te_last_work(te_handle)
+        ex_pass = te.te_last_pass_work(te_handle)
     finally:
         te.te_set_search(te_handle, True)
     got = te.te_estimate(te_handle, ds, w.instances, w.k, want_counts=True)
     sw_pairs, _, swept1 = te.te_last_work(te_handle)
+    (p1, p2), (c1, c2) = te.te_last_pass_work(te_handle)
     torch.cuda.synchronize()
     assert not swept0 and swept1
     assert torch.equal(ref["counts"], got["counts"]) and torch.equal(ref["eps"], got["eps"])
     assert torch.max(torch.abs(ref["te"] - got["te"])).item() <= 1e-9
     assert 0 < sw_pairs <= ex_pairs
+    # work by pass: N^2 per pass for the exhaustive search; the sweep's two passes add up to its
+    # total and both took cycles
+    assert ex_pass == ((ex_pairs // 2, ex_pairs // 2), (0, 0))
+    assert p1 + p2 == sw_pairs and p1 > 0 and p2 > 0
+    assert c1 > 0 and c2 > 0
 
 
 def test_plan_reuse_follows_the_inputs(te_handle):
