@@ -128,13 +128,21 @@ __device__ __forceinline__ void bknn_group(const float* __restrict__ s, const in
             mm[m][q][2] = absmax_join<d>(ma[q][2], cz);
             mm[m][q][3] = absmax_join<d>(ma[q][3], cw);
         }
+        if constexpr (d >= 4) {  // wide members: insert before the next member's loads (registers)
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) topk_push(t[m][q], mm[m][q][e]);
+        }
     }
+    if constexpr (d < 4) {
 #pragma unroll
-    for (int m = 0; m < M; ++m)
+        for (int m = 0; m < M; ++m)
 #pragma unroll
-        for (int q = 0; q < Q; ++q)
+            for (int q = 0; q < Q; ++q)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) topk_push(t[m][q], mm[m][q][e]);
+                for (int e = 0; e < 4; ++e) topk_push(t[m][q], mm[m][q][e]);
+    }
 }
 
 // pass 1 over groups [g0, g1) in direction dir (as knn_range in te_sweep.cuh)
