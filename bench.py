@@ -267,6 +267,11 @@ def bench_ours(args):
     dev = torch.device("cuda", local)
     if ws > 1:
         dist.init_process_group("nccl", device_id=dev)
+    # one rank (re)builds the library if it is stale; the others wait and then find it current
+    if rank == 0:
+        build.build()
+    if ws > 1:
+        dist.barrier()
     build.build()
     spec = WORKLOADS[args.workload]
     w = load_workload(spec)
