@@ -89,7 +89,8 @@ te_status te_create(te_handle** out, int32_t device);
 void te_destroy(te_handle* h);
 
 /* Message of the last failed call on this handle ("" after success). Valid until the next
- * call on the handle. A NULL handle returns the message of the last failed te_create. */
+ * call on the handle. A NULL handle returns the message of the calling thread's last failed
+ * te_create. */
 const char* te_last_error(const te_handle* h);
 
 /* Synchronise `stream` and report device-side flags raised since the previous check

@@ -34,7 +34,7 @@ constexpr int kSmemCapBytes = 64 * 1024;  // reference tile budget of the batche
 constexpr int kSweepSmemMaxBytes = 160 * 1024;  // sweep mode: room for whole query blocks per tile
 constexpr int64_t kResidentMaxBytes = 200 * 1024;  // sweep mode: whole instances in shared memory
 
-std::string g_create_error;
+thread_local std::string g_create_error;  // per host thread: concurrent te_create calls do not race
 
 // digamma at positive integers in FP64: -gamma + H_{n-1} below 16, the asymptotic expansion
 // ln n - 1/(2n) - sum_k B_2k / (2k n^2k) (six terms, error < 1e-16) from 16 on
