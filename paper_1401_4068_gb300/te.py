@@ -127,6 +127,16 @@ def _need(t: torch.Tensor, dtype, name: str):
         raise ValueError(f"{name} must be contiguous")
 
 
+def _need_out(t, dtype, numel: int, dev, name: str):
+    """A caller-supplied output: a contiguous CUDA tensor of `dtype` on `dev` with room for
+    `numel` elements (the library writes that many)."""
+    _need(t, dtype, name)
+    if t.device != torch.device(dev):
+        raise ValueError(f"{name} must be on {dev}, got {t.device}")
+    if t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, the call writes {numel}")
+
+
 class Handle:
     """Owner of a ``te_handle*`` (device workspace, cached plans and graphs)."""
 
@@ -272,6 +282,8 @@ def te_estimate(h: Handle, series: Sequence[DeviceSeries], instances: Sequence, 
             npts += series[int(it.series)].src.shape[0] * int(it.window)
     if te is None:
         te = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
+    else:
+        _need_out(te, torch.float64, n, dev, "te")
     err = torch.full((n,), float("nan"), dtype=torch.float64, device=dev) if want_err else None
     # sentinels (-1, NaN): a point the library failed to write can never pass for a result
     counts = torch.full((3 * npts,), -1, dtype=torch.int32, device=dev) if want_counts else None
@@ -294,6 +306,10 @@ def te_surrogate_test(h: Handle, series: Sequence[DeviceSeries], t_starts: Seque
         out = {"te_orig": torch.full((ns, nt), float("nan"), dtype=torch.float64, device=dev),
                "te_surr": torch.full((ns, nt, max(S, 1)), float("nan"), dtype=torch.float64, device=dev),
                "p": torch.full((ns, nt), float("nan"), dtype=torch.float64, device=dev)}
+    else:
+        _need_out(out["te_orig"], torch.float64, ns * nt, dev, "te_orig")
+        _need_out(out["te_surr"], torch.float64, ns * nt * max(S, 0), dev, "te_surr")
+        _need_out(out["p"], torch.float64, ns * nt, dev, "p")
     h.check(h.lib.te_surrogate_test(h.h, ser, ns, C.cast(ts, C.c_void_p), nt, int(window),
                                     int(S), int(k), _ptr(out["te_orig"]), _ptr(out["te_surr"]),
                                     _ptr(out["p"]), _stream(stream)))
@@ -349,6 +365,10 @@ def te_delay_scan(h: Handle, series: DeviceSeries, t_starts: Sequence[int], wind
         out = {"te": torch.full((max(n_u, 1), max(n_t, 1)), float("nan"), dtype=torch.float64, device=dev),
                "p": torch.full((max(n_u, 1), max(n_t, 1)), float("nan"), dtype=torch.float64, device=dev),
                "u_best": torch.full((max(n_t, 1),), -1, dtype=torch.int32, device=dev)}
+    else:
+        _need_out(out["te"], torch.float64, max(n_u, 0) * n_t, dev, "te")
+        _need_out(out["p"], torch.float64, max(n_u, 0) * n_t, dev, "p")
+        _need_out(out["u_best"], torch.int32, n_t, dev, "u_best")
     h.check(h.lib.te_delay_scan(h.h, ser, C.cast(ts, C.c_void_p), n_t, int(window), int(u_lo), int(u_hi),
                                 int(S), int(k), _ptr(out["te"]), _ptr(out["p"]), _ptr(out["u_best"]),
                                 _stream(stream)))

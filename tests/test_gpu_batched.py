@@ -224,6 +224,25 @@ def test_argument_errors_launch_nothing(te_handle):
     assert out.item() == 7.0
 
 
+def test_caller_outputs_are_checked_before_any_launch(te_handle):
+    w = I.config(3, n_t=2, S=3)
+    ds = te.to_device(w.series)
+    n = len(w.instances)
+    for bad, err in ((torch.zeros(n - 1, dtype=torch.float64, device="cuda"), ValueError),
+                     (torch.zeros(n, dtype=torch.float32, device="cuda"), TypeError),
+                     (torch.zeros(2 * n, dtype=torch.float64, device="cuda")[::2], ValueError),
+                     (torch.zeros(n, dtype=torch.float64), TypeError)):
+        with pytest.raises(err):
+            te.te_estimate(te_handle, ds, w.instances, w.k, te=bad)
+    out = {"te_orig": torch.zeros((1, 2), dtype=torch.float64, device="cuda"),
+           "te_surr": torch.zeros((1, 2, 2), dtype=torch.float64, device="cuda"),  # S = 3 needed
+           "p": torch.zeros((1, 2), dtype=torch.float64, device="cuda")}
+    with pytest.raises(ValueError, match="te_surr"):
+        te.te_surrogate_test(te_handle, ds, w.t_starts[0], w.window, w.S, w.k, out=out)
+    torch.cuda.synchronize()
+    assert float(out["te_surr"].abs().sum()) == 0.0
+
+
 def test_per_instance_launch_mode_is_bit_identical(te_handle):
     w = I.config(4, n_pairs=5, n_t=2)
     ds = te.to_device(w.series)
