@@ -192,11 +192,13 @@ def te_embed(h: Handle, src: torch.Tensor, tgt: torch.Tensor, d: int, tau: int, 
     N = R * window
     D = 1 + 2 * d
     ld = ld or ((N + 3) // 4) * 4
+    if tgt.shape != src.shape:
+        raise ValueError(f"src {tuple(src.shape)} and tgt {tuple(tgt.shape)} differ")
     if points is None:
         points = torch.full((D, ld), float("nan"), dtype=torch.float32, device=src.device)
-    _need(points, torch.float32, "points")
+    _need_out(points, torch.float32, D * ld, src.device, "points")
     if perm is not None:
-        _need(perm, torch.int32, "perm")
+        _need_out(perm, torch.int32, R, src.device, "perm")
     p = te_params(d, tau, u, 0, t_start, window)
     h.check(h.lib.te_embed(h.h, _ptr(src), _ptr(tgt), R, T, C.byref(p), _ptr(perm), _ptr(points),
                            ld, _stream(stream)))
@@ -205,9 +207,10 @@ def te_embed(h: Handle, src: torch.Tensor, tgt: torch.Tensor, d: int, tau: int, 
 
 def te_knn_maxnorm(h: Handle, points: torch.Tensor, N: int, D: int, ld: int, k: int,
                    eps: Optional[torch.Tensor] = None, want_nn: bool = False, stream=None):
-    _need(points, torch.float32, "points")
+    _need_out(points, torch.float32, D * ld, points.device, "points")
     if eps is None:
         eps = torch.full((N,), float("nan"), dtype=torch.float32, device=points.device)
+    _need_out(eps, torch.float32, N, points.device, "eps")
     nn = torch.full((N, k), -1, dtype=torch.int32, device=points.device) if want_nn else None
     h.check(h.lib.te_knn_maxnorm(h.h, _ptr(points), N, D, ld, k, _ptr(eps), _ptr(nn),
                                  _stream(stream)))
@@ -216,10 +219,11 @@ def te_knn_maxnorm(h: Handle, points: torch.Tensor, N: int, D: int, ld: int, k: 
 
 def te_range_count(h: Handle, points: torch.Tensor, N: int, d_y: int, d_x: int, ld: int,
                    eps: torch.Tensor, counts: Optional[torch.Tensor] = None, stream=None):
-    _need(points, torch.float32, "points")
-    _need(eps, torch.float32, "eps")
+    _need_out(points, torch.float32, (1 + d_y + d_x) * ld, points.device, "points")
+    _need_out(eps, torch.float32, N, points.device, "eps")
     if counts is None:
         counts = torch.full((3, N), -1, dtype=torch.int32, device=points.device)
+    _need_out(counts, torch.int32, 3 * N, points.device, "counts")
     h.check(h.lib.te_range_count(h.h, _ptr(points), N, d_y, d_x, ld, _ptr(eps), _ptr(counts),
                                  _stream(stream)))
     return counts

@@ -110,8 +110,13 @@ def test_knn_argument_errors(te_handle):
         te.te_knn_maxnorm(te_handle, dev, 10, 3, ld, 10)   # k = N
     with pytest.raises(te.TEError, match="TE_EINVAL"):
         te.te_knn_maxnorm(te_handle, dev, 10, 3, ld, 17)   # k > 16
+    wide = torch.zeros((33, ld), dtype=torch.float32, device="cuda")
     with pytest.raises(te.TEError, match="TE_EINVAL"):
-        te.te_knn_maxnorm(te_handle, dev, 10, 33, ld, 4)   # D > 32
+        te.te_knn_maxnorm(te_handle, wide, 10, 33, ld, 4)  # D > 32
+    with pytest.raises(ValueError, match="points"):        # the binding: 3 x ld floats for D = 5
+        te.te_knn_maxnorm(te_handle, dev, 10, 5, ld, 4)
+    with pytest.raises(ValueError, match="eps"):
+        te.te_knn_maxnorm(te_handle, dev, 10, 3, ld, 4, eps=torch.zeros(9, dtype=torch.float32, device="cuda"))
     with pytest.raises(te.TEError, match="TE_EINVAL"):
         te.te_knn_maxnorm(te_handle, dev, 10, 3, 6, 4)     # ld not a multiple of 4
 
