@@ -465,13 +465,15 @@ def bench_ours(args):
         else:
             wsub = I.Workload(w.name, w.series, w.instances[: args.per_launch_instances], w.k)
 
+        sub_arr = te.instance_array(wsub.instances)
+
         def sub_step(o=None):
             if scan:
                 sr = scan_range(wsub)
                 return te.te_delay_scan(h, ds[0], wsub.t_starts[0], wsub.window, sr[0], sr[1], wsub.S, wsub.k)
             if surrogate:
                 return te.te_surrogate_test(h, ds, wsub.t_starts[0], wsub.window, wsub.S, wsub.k)
-            return te.te_estimate(h, ds, wsub.instances, wsub.k)
+            return te.te_estimate(h, ds, sub_arr, wsub.k)
 
         res = {}
         for mode in (True, False):
