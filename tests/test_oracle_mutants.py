@@ -39,6 +39,14 @@ MUTANTS = [
     ("permutation on the target", "const float* y = tgt + (size_t)r * T;",
      "const float* y = tgt + (size_t)rs * T;"),
     ("transposed difference operand", "fabsf(a[c] - b[c])", "fabsf(a[c] - b[c - (c > 0)])"),
+    ("surrogate row of the permutation table", "perm = s->perms + (size_t)in->perm * s->R;",
+     "perm = s->perms + (size_t)in->perm;"),
+    ("wrong series of an instance", "const oracle_series* s = &jb->series[in->series];",
+     "const oracle_series* s = &jb->series[0];"),
+    ("counts block offset", "jb->counts + 3 * jb->off[i]", "jb->counts + jb->off[i]"),
+    ("point offsets from the first series", "off[i] + (int64_t)series[inst[i].series].R * inst[i].window",
+     "off[i] + (int64_t)series[0].R * inst[i].window"),
+    ("surrogate pairing on the original", "if (in->perm >= 0) {", "if (in->perm > 0) {"),
 ]
 
 
@@ -79,9 +87,56 @@ def _run_pins(lib) -> list:
         ref = sp_digamma(2) + np.mean(sp_digamma(c[0] + 1) - sp_digamma(c[1] + 1) - sp_digamma(c[2] + 1))
         if abs(te - ref) > 1e-12: fails.append("te-table")
         if oracle.pvalue(0.5, np.array([0.1, 0.5, 0.7, 0.2])) != 0.5: fails.append("pvalue")
+        fails += batch_dispatch_failures()
     finally:
         oracle._lib = saved
     return fails
+
+
+def batch_dispatch_failures() -> list:
+    """te_batch against physically shuffled trials (Fig. 3: a surrogate pairs the target's
+    repetitions with reordered source repetitions).  Two series of different trial counts and
+    delays, instances in mixed order with different windows; for each one the expected values
+    come from the source array whose rows were reordered with numpy (row r of the surrogate's
+    source = source row perm[r]) and analysed as an original, so no permutation offset, series
+    index or output offset of the batch code is involved."""
+    fails = []
+    rng = np.random.default_rng(20140728)
+    Ser = type("Ser", (), {})
+    series = []
+    for R, T, d, u in ((5, 30, 1, 2), (6, 28, 2, 3)):
+        s = Ser()
+        s.src = rng.standard_normal((R, T)).astype(np.float32)
+        s.tgt = rng.standard_normal((R, T)).astype(np.float32)
+        s.d, s.tau, s.u = d, 1, u
+        s.perms = np.stack([rng.permutation(R) for _ in range(3)]).astype(np.int32)
+        series.append(s)
+    Inst = type("Inst", (), {})
+    spec = [(1, 9, 3, 2), (0, 8, 4, -1), (0, 12, 3, 0), (1, 9, 3, 1), (0, 8, 4, 2), (1, 14, 5, -1), (0, 8, 4, 1)]
+    insts = []
+    for si, t, W, p in spec:
+        it = Inst()
+        it.series, it.t_start, it.window, it.perm = si, t, W, p
+        insts.append(it)
+    k = 2
+    te, counts, eps = oracle.te_batch(series, insts, k, n_threads=2, want_counts=True)
+    off = 0
+    for i, it in enumerate(insts):
+        s = series[it.series]
+        src = s.src if it.perm < 0 else s.src[s.perms[it.perm]]
+        pts = oracle.embed(src, s.tgt, s.d, s.tau, s.u, it.t_start, it.window, None)
+        N = pts.shape[0]
+        te_i, eps_i, c_i = oracle.te_points(pts, s.d, s.d, k)
+        if te[i] != te_i: fails.append(f"batch-te[{i}]")
+        if not np.array_equal(counts[3 * off:3 * (off + N)].reshape(3, N), c_i): fails.append(f"batch-counts[{i}]")
+        if not np.array_equal(eps[off:off + N], eps_i): fails.append(f"batch-eps[{i}]")
+        off += N
+    if off != eps.shape[0]: fails.append("batch-size")
+    return fails
+
+
+def test_batch_dispatch_pin():
+    assert batch_dispatch_failures() == []
 
 
 def _build(tmp_path, find, repl):
