@@ -220,15 +220,21 @@ te_status te_set_search(te_handle* h, int32_t mode);
  * `swept` (nullable) is 1 when the sweep ran. */
 te_status te_last_work(te_handle* h, uint64_t* pairs, uint64_t* ops, int32_t* swept);
 
-/* Target-part sharing in the sorted sweep (enable = 1, the default; results are identical):
- * estimates whose joint points share the target part y_t, y- (same target series, repetitions,
- * window start, window, d and tau; they differ only in the source part x-: the original and its
- * trial-shuffled surrogates of Fig. 3, and every scanned delay u of Eq. 5) are processed in
- * bundles of up to 3 that fit shared memory together. A bundle is staged once and the target
- * part of every distance and count is computed once for all of its members. The paper computes
- * each surrogate separately; this is exact because max is exact: each member sees the same FP32
- * differences the unshared search computes. Applies with k <= 4 to one embedding dimension per
- * batch (the most frequent among shareable estimates); every other estimate runs unshared. */
+/* Target-part sharing in the sorted sweep (results are identical in every mode): estimates whose
+ * joint points share the target part y_t, y- (same target series, repetitions, window start,
+ * window, d and tau; they differ only in the source part x-: the original and its trial-shuffled
+ * surrogates of Fig. 3, and every scanned delay u of Eq. 5) compute the target part of each
+ * distance and count once for several estimates. The paper computes each surrogate separately;
+ * this is exact because max is exact: each estimate sees the same FP32 differences the unshared
+ * search computes.
+ *   enable = 1 (default): groups of at least 8 such estimates with d = 2..8 run one estimate per
+ *     lane (a warp takes one query point for 32 estimates; a reference whose target-part distance
+ *     already reaches every lane's current radius is skipped for all 32 before any source
+ *     coordinate is read); smaller groups with d <= 5 run in bundles of up to 3 staged together in
+ *     shared memory (one embedding dimension per batch, the most frequent among them).
+ *   enable = 2: bundles only (no lane kernel).
+ *   enable = 0: no sharing.
+ * Sharing applies with k <= 4; every other estimate runs unshared. TE_EINVAL for other values. */
 te_status te_set_sharing(te_handle* h, int32_t enable);
 
 /* FP32 operations the kernels of the last te_estimate / te_surrogate_test / te_delay_scan call
@@ -236,6 +242,11 @@ te_status te_set_sharing(te_handle* h, int32_t enable);
  * ops without sharing). `bundles` (nullable): the number of bundles formed. The sweep's counters
  * are read from the device (synchronises the device). */
 te_status te_last_alu_ops(te_handle* h, uint64_t* ops, int32_t* bundles);
+
+/* How the last te_estimate / te_surrogate_test / te_delay_scan call ran its estimates (a delay
+ * scan counts every (delay, estimate) pair): paths[0] = on the lane kernel (one estimate per
+ * lane), paths[1] = in bundles of up to 3, paths[2] = unshared. `paths` has three entries. */
+te_status te_last_paths(te_handle* h, int32_t* paths);
 
 /* The work of the last te_estimate / te_surrogate_test / te_delay_scan call split by pass:
  * pairs[0], pairs[1] = (query, reference) pair evaluations of pass 1 (the k-th neighbour search,

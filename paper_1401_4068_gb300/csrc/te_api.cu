@@ -33,6 +33,11 @@ constexpr int kMaxBundleD = 5;        // target-part sharing
 constexpr int kSmemCapBytes = 64 * 1024;  // reference tile budget of the batched kernel
 constexpr int kSweepSmemMaxBytes = 160 * 1024;  // sweep mode: room for whole query blocks per tile
 constexpr int64_t kResidentMaxBytes = 200 * 1024;  // sweep mode: whole instances in shared memory
+// device word array: [0] batched-kernel queue, [1] flags, [2..3] bundle-kernel queues, one lane-kernel
+// queue per d (kLaneMinD .. kLaneMaxD), then one queue per instance for per-instance launches
+constexpr int kWordLaneQueue = 4;
+constexpr int64_t kLaneXMaxBytes = (int64_t)16 << 30;  // member-minor source arrays of the lane kernel
+constexpr int kWordPerInstance = kWordLaneQueue + te::kLaneMaxD - te::kLaneMinD + 1;
 
 thread_local std::string g_create_error;  // per host thread: concurrent te_create calls do not race
 
@@ -121,6 +126,18 @@ struct Plan {
     std::vector<int32_t> members;
     int bd = 0, bgrid = 0, tgrid = 0, n_bundled = 0, n_bres = 0;
     size_t bsmem = 0, tsmem = 0;   // dynamic shared memory of the resident / tiled bundle launches
+    // lane kernel (one estimate per lane): groups, their members, work items ordered by d
+    // (items of d: litems[lane_begin[d] .. lane_begin[d + 1] - 1]) and the grid per d
+    std::vector<te::LaneGroup> lgroups;
+    std::vector<te::LaneItem> litems;
+    std::vector<int32_t> lmembers;
+    int64_t tp_total = 0;          // float2 entries of the sorted target parts
+    std::vector<te::LaneXBlock> xblocks;
+    int64_t x_total = 0, x_max = 0;  // floats of all / the largest member-minor source array
+    int lane_max_np = 0;
+    int lane_begin[te::kLaneMaxD + 2] = {0};
+    int lane_grid[te::kLaneMaxD + 1] = {0};
+    int n_lane = 0;                // estimates on the lane kernel
     uint64_t table_hash = 0;  // of the device tables (instances, items, bundles): part of the graph key
 };
 
@@ -166,10 +183,11 @@ struct te_handle {
     int tune_gen = 0;                                   // bumped whenever `tuned` changes
     bool per_instance = false;  // one launch per instance instead of one persistent launch
     int search_mode = 1;        // 1: sorted sweep where it applies, 0: exhaustive search
-    bool sharing = true;        // bundles of estimates with one target part (sweep mode)
+    int sharing = 1;            // 1: lanes and bundles, 2: bundles only, 0: no target-part sharing
     bool last_sweep = false;
     uint64_t last_pairs = 0, last_ops = 0;
     int last_bundled = 0;
+    int last_paths[3] = {0, 0, 0};  // estimates on the lane kernel, in bundles, unshared
 
     DevBuf<InstDesc> d_insts;
     DevBuf<WorkItem> d_items;
@@ -183,6 +201,12 @@ struct te_handle {
     DevBuf<unsigned long long> d_exec;
     DevBuf<WorkItem> d_bitems;
     DevBuf<int32_t> d_members;
+    DevBuf<te::LaneGroup> d_lgroups;
+    DevBuf<te::LaneItem> d_litems;
+    DevBuf<int32_t> d_lmembers, d_lrw;
+    DevBuf<float2> d_tpart;
+    DevBuf<te::LaneXBlock> d_lxb;
+    DevBuf<float> d_lx;
     HostBuf<unsigned char> h_stage;
     int workspace_gen = 0;
 
@@ -428,6 +452,134 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
     const int want_items = 4 * h->sm_count;
     int max_parts = 1;
     int n_parts = 0;
+    // one estimate per lane: groups of at least kLaneMinMembers estimates with one target part
+    // (target series, repetitions, window start, window, d, tau) and d in kLaneMinD .. kLaneMaxD;
+    // each member has one partial sum per block of kLaneQB sorted query positions. Blocks of 32
+    // members read their source part from member-minor arrays (LaneXBlock), shared by blocks with
+    // the same source series and pairings; past kLaneXMaxBytes of such arrays no lanes are used.
+    std::vector<char> laned(n_inst, 0);
+    if (sweep && h->sharing == 1 && !h->per_instance && ks == 5) {
+        typedef std::tuple<const float*, int, int, int, int, int, int> TK;
+        std::map<TK, std::vector<int>> by_target;
+        std::vector<TK> korder;
+        for (int i = 0; i < n_inst; ++i) {
+            const InstDesc& I = P->insts[i];
+            if (I.d < te::kLaneMinD || I.d > te::kLaneMaxD) continue;
+            const TK key = std::make_tuple(I.tgt, I.T, I.R, I.t_start, I.W, I.d, I.tau);
+            auto f = by_target.find(key);
+            if (f == by_target.end()) {
+                korder.push_back(key);
+                f = by_target.emplace(key, std::vector<int>()).first;
+            }
+            f->second.push_back(i);
+        }
+        // X blocks: one per distinct (R, T, the 32 lanes' source series and pairings), columns the
+        // union of the samples its groups read
+        std::vector<te::LaneXBlock> xb;
+        std::map<std::vector<uintptr_t>, int> xsig;
+        std::vector<std::vector<int>> cand;     // member lists of the lane groups
+        std::vector<std::vector<int>> cand_xb;  // their blocks' X block
+        for (const auto& key : korder) {
+            const std::vector<int>& v = by_target[key];
+            if ((int)v.size() < te::kLaneMinMembers) continue;
+            std::vector<int> blocks;
+            for (size_t b = 0; b * 32 < v.size(); ++b) {
+                std::vector<uintptr_t> sig;
+                const InstDesc& I0 = P->insts[v[0]];
+                sig.push_back((uintptr_t)I0.R);
+                sig.push_back((uintptr_t)I0.T);
+                int cmin = INT32_MAX, cmax = INT32_MIN;
+                for (int l = 0; l < 32; ++l) {
+                    const InstDesc& I = P->insts[v[std::min(v.size() - 1, b * 32 + (size_t)l)]];
+                    sig.push_back((uintptr_t)I.src);
+                    sig.push_back((uintptr_t)I.perm);
+                    cmin = std::min(cmin, I.t_start - I.u - (I.d - 1) * I.tau);
+                    cmax = std::max(cmax, I.t_start + I.W - 1 - I.u);
+                }
+                auto f = xsig.find(sig);
+                if (f == xsig.end()) {
+                    te::LaneXBlock X{};
+                    X.R = I0.R;
+                    X.T = I0.T;
+                    X.t0 = cmin;
+                    X.ncols = cmax - cmin + 1;
+                    for (int l = 0; l < 32; ++l) {
+                        const InstDesc& I = P->insts[v[std::min(v.size() - 1, b * 32 + (size_t)l)]];
+                        X.src[l] = I.src;
+                        X.perm[l] = I.perm;
+                    }
+                    f = xsig.emplace(sig, (int)xb.size()).first;
+                    xb.push_back(X);
+                } else {
+                    te::LaneXBlock& X = xb[f->second];
+                    const int hi = std::max(X.t0 + X.ncols - 1, cmax);
+                    X.t0 = std::min(X.t0, cmin);
+                    X.ncols = hi - X.t0 + 1;
+                }
+                blocks.push_back(f->second);
+            }
+            cand.push_back(v);
+            cand_xb.push_back(blocks);
+        }
+        int64_t xtotal = 0, xmax = 0;
+        for (auto& X : xb) {
+            X.off = xtotal;
+            const int64_t n = (int64_t)X.R * X.ncols * 32;
+            xtotal += n;
+            xmax = std::max(xmax, n);
+        }
+        if (xtotal * (int64_t)sizeof(float) > kLaneXMaxBytes) cand.clear();
+        for (size_t g = 0; g < cand.size(); ++g) {
+            const std::vector<int>& v = cand[g];
+            const InstDesc& I0 = P->insts[v[0]];
+            te::LaneGroup G{};
+            G.tgt = I0.tgt;
+            G.R = I0.R;
+            G.T = I0.T;
+            G.W = I0.W;
+            G.t_start = I0.t_start;
+            G.N = I0.N;
+            G.d = I0.d;
+            G.tau = I0.tau;
+            G.mem_off = (int)P->lmembers.size();
+            G.n_mem = (int)v.size();
+            const int NP = (I0.N + 31) & ~31;
+            G.tp_off = P->tp_total;
+            P->tp_total += (int64_t)((I0.d + 2) / 2) * NP;
+            P->lane_max_np = std::max(P->lane_max_np, NP);
+            const int nqb = (I0.N + te::kLaneQB - 1) / te::kLaneQB;
+            for (int i : v) {
+                InstDesc& I = P->insts[i];
+                P->lmembers.push_back(i);
+                laned[i] = 1;
+                I.item_begin = 0;
+                I.n_items = 0;
+                I.warp_mode = 0;
+                I.part_begin = n_parts;
+                I.n_parts = nqb;
+                n_parts += nqb;
+                max_parts = std::max(max_parts, nqb);
+            }
+            P->lgroups.push_back(G);
+            P->n_lane += (int)v.size();
+        }
+        if (!cand.empty()) {
+            P->xblocks = xb;
+            P->x_total = xtotal;
+            P->x_max = xmax;
+        }
+        for (int d = te::kLaneMinD; d <= te::kLaneMaxD; ++d) {
+            P->lane_begin[d] = (int)P->litems.size();
+            for (int g = 0; g < (int)P->lgroups.size(); ++g) {
+                const te::LaneGroup& G = P->lgroups[g];
+                if (G.d != d) continue;
+                for (int mb = 0; mb * 32 < G.n_mem; ++mb)
+                    for (int q0 = 0; q0 < G.N; q0 += te::kLaneQB)
+                        P->litems.push_back(te::LaneItem{g, mb, q0, cand_xb[g][mb]});
+            }
+        }
+        P->lane_begin[te::kLaneMaxD + 1] = (int)P->litems.size();
+    }
     // target-part sharing: estimates with one target part (target series, repetitions, window
     // start, window, d, tau) form bundles of up to kBundleMax (no bundle of one), processed by the
     // bundle kernel; one embedding dimension per batch. A bundle that fits kResidentMaxBytes is
@@ -441,6 +593,7 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
         std::map<std::tuple<const float*, int, int, int, int, int, int>, std::vector<int>> by_target;
         for (int i = 0; i < n_inst; ++i) {
             const InstDesc& I = P->insts[i];
+            if (laned[i]) continue;
             by_target[std::make_tuple(I.tgt, I.T, I.R, I.t_start, I.W, I.d, I.tau)].push_back(i);
         }
         auto resident_bytes = [](const InstDesc& I) {
@@ -524,7 +677,7 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
         I.strips = 1;
         I.npad = I.N;
         I.strip_off = 0;
-        if (bundled[i]) continue;
+        if (bundled[i] || laned[i]) continue;
         const bool fits = (int64_t)((I.N + 3) & ~3) * (1 + 2 * I.d) <= P->smem_floats;
         I.warp_mode = (sweep && fits && !h->per_instance) ? 1 : 0;
     }
@@ -561,6 +714,7 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
                 const bool tiled_alone = !bundled[i] && I.warp_mode == 0 && te::kStripPoints % per == 0 &&
                                          (int64_t)te::kStripPoints * (1 + 2 * I.d) * 4 <= kSweepSmemMaxBytes;
                 if (lag != k2lag || !(resident_alone || resident_bundle || tiled_bundle || tiled_alone)) ok = false;
+                if (laned[i]) ok = false;  // the lane kernel sweeps one key order
             }
             // strips of kStripPoints, for groups of 4 strips or more (shorter strips were measured
             // slower: a C3 group of 1200 points in 4 strips took 66.7 ms instead of 46.9 ms; the
@@ -585,6 +739,7 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
             if (S > 1) strip_total += S + 1;
         }
         P->strip_total = strip_total;
+        for (auto& G : P->lgroups) G.sort_off = P->insts[P->lmembers[G.mem_off]].sort_off;
     }
     // tiled bundles: one work item per block of kBundleThreads * kBundleQ sorted positions
     {
@@ -606,7 +761,7 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
     // partial-sum ranges: a staged-whole estimate is cut into items of warp blocks (32 * qpt
     // sorted positions), any other into CTA query blocks
     for (int i : order) {
-        if (bundled[i]) continue;
+        if (bundled[i] || laned[i]) continue;
         InstDesc& I = P->insts[i];
         I.item_begin = (int)P->items.size();
         I.part_begin = n_parts;
@@ -631,7 +786,7 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
     // CTAs unless a shape was set or tuned for this signature)
     bool all_warp = !P->items.empty();
     for (int i = 0; i < n_inst; ++i)
-        if (!bundled[i] && !P->insts[i].warp_mode) all_warp = false;
+        if (!bundled[i] && !laned[i] && !P->insts[i].warp_mode) all_warp = false;
     if (sweep && !h->per_instance && all_warp && dlo == dhi && dlo <= 2 && ks == 5) {
         P->var.warp_only = true;
         const bool shaped = h->cfg_threads || h->tuned.find(shape_signature(P->insts, ks)) != h->tuned.end();
@@ -641,7 +796,9 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
     // bound on the summation error relative to sum |terms| (see te_estimate in the header):
     // 3*qpt float-float additions per thread (<= 2^-46 each), table rounding (2^-47), FP64
     // reductions over threads and items
-    P->err_coef = 3.0 * qpt * 0x1p-46 + 0x1p-47 + (threads + max_parts + 64) * 0x1p-52;
+    // (a lane of the lane kernel adds 3 terms per query for kLaneQB / kLaneWarps queries)
+    const int ff_terms = std::max(3 * qpt, P->n_lane ? 3 * (te::kLaneQB / te::kLaneWarps) : 0);
+    P->err_coef = ff_terms * 0x1p-46 + 0x1p-47 + (threads + max_parts + 64) * 0x1p-52;
     const void* fn = te::batched_kernel_ptr(P->var);
     if (!fn) return h->fail(TE_ENOTIMPL, "no kernel variant for d=%d..%d ks=%d qpt=%d", dlo, dhi, ks, qpt);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smem);
@@ -665,11 +822,26 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
         if (bper < 1) return h->fail(TE_ENOTIMPL, "bundle kernel does not fit: smem=%zu", smem);
         (tiled ? P->tgrid : P->bgrid) = (int)std::min<int64_t>((int64_t)bper * h->sm_count, n);
     }
+    for (int d = te::kLaneMinD; d <= te::kLaneMaxD; ++d) {
+        const int n = P->lane_begin[d + 1] - P->lane_begin[d];
+        if (n <= 0) continue;
+        const void* lf = te::lane_kernel_ptr(d, ks);
+        if (!lf) return h->fail(TE_ENOTIMPL, "no lane kernel for d=%d ks=%d", d, ks);
+        int lper = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lper, lf, te::kLaneThreads, 0)) != cudaSuccess)
+            return h->cuda_fail(e, "occupancy query (lanes)");
+        if (lper < 1) return h->fail(TE_ENOTIMPL, "lane kernel does not fit");
+        P->lane_grid[d] = (int)std::min<int64_t>((int64_t)lper * h->sm_count, n);
+    }
     uint64_t th = 1469598103934665603ull;
     th = fnv(th, P->insts.data(), P->insts.size() * sizeof(InstDesc));
     th = fnv(th, P->items.data(), P->items.size() * sizeof(WorkItem));
     th = fnv(th, P->bitems.data(), P->bitems.size() * sizeof(WorkItem));
     th = fnv(th, P->members.data(), P->members.size() * sizeof(int32_t));
+    th = fnv(th, P->lgroups.data(), P->lgroups.size() * sizeof(te::LaneGroup));
+    th = fnv(th, P->litems.data(), P->litems.size() * sizeof(te::LaneItem));
+    th = fnv(th, P->lmembers.data(), P->lmembers.size() * sizeof(int32_t));
+    th = fnv(th, P->xblocks.data(), P->xblocks.size() * sizeof(te::LaneXBlock));
     P->table_hash = th;
     (void)nmax;
     return TE_OK;
@@ -679,7 +851,7 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
 // setting that shapes a plan equal those of the previous call byte for byte, else rebuilt.
 te_status cached_plan(te_handle* h, const te_series* series, int n_series, const te_instance* inst, int n_inst,
                       int k, Plan** out) {
-    std::vector<int> cfg = {k, h->search_mode, h->sharing ? 1 : 0, h->per_instance ? 1 : 0, h->cfg_threads,
+    std::vector<int> cfg = {k, h->search_mode, h->sharing, h->per_instance ? 1 : 0, h->cfg_threads,
                             h->cfg_qpt, h->tune_gen, h->sm_count};
     const bool hit = h->pc_valid && h->pc_cfg == cfg && (int)h->pc_series.size() == n_series &&
                      (int)h->pc_inst.size() == n_inst &&
@@ -704,15 +876,29 @@ te_status upload_tables(te_handle* h, const Plan& P, cudaStream_t stream) {
     const size_t bi = P.insts.size() * sizeof(InstDesc), bt = P.items.size() * sizeof(WorkItem);
     const size_t bg = P.groups.size() * sizeof(te::SortGroup);
     const size_t bb = P.bitems.size() * sizeof(WorkItem), bm = P.members.size() * sizeof(int32_t);
+    const size_t blg = P.lgroups.size() * sizeof(te::LaneGroup), bli = P.litems.size() * sizeof(te::LaneItem);
+    const size_t blm = P.lmembers.size() * sizeof(int32_t), blx = P.xblocks.size() * sizeof(te::LaneXBlock);
+    const size_t ol = bi + bt + bg + bb + bm;  // lane tables follow (8-byte aligned: every size above is)
     cudaError_t e;
     if ((e = cudaEventSynchronize(h->upload_done)) != cudaSuccess) return h->cuda_fail(e, "staging reuse");
-    if ((e = h->h_stage.ensure(bi + bt + bg + bb + bm)) != cudaSuccess) return h->fail(TE_ENOMEM, "pinned staging");
+    if ((e = h->h_stage.ensure(ol + blg + bli + blm + blx + 64)) != cudaSuccess)
+        return h->fail(TE_ENOMEM, "pinned staging");
     unsigned char* hs = h->h_stage.p;
     std::memcpy(hs, P.insts.data(), bi);
     if (bt) std::memcpy(hs + bi, P.items.data(), bt);
     if (bg) std::memcpy(hs + bi + bt, P.groups.data(), bg);
     if (bb) std::memcpy(hs + bi + bt + bg, P.bitems.data(), bb);
     if (bm) std::memcpy(hs + bi + bt + bg + bb, P.members.data(), bm);
+    const size_t olg = (ol + 7) & ~(size_t)7, oli = olg + blg, olm = oli + bli, olx = (olm + blm + 7) & ~(size_t)7;
+    if (blg) std::memcpy(hs + olg, P.lgroups.data(), blg);
+    if (bli) std::memcpy(hs + oli, P.litems.data(), bli);
+    if (blm) std::memcpy(hs + olm, P.lmembers.data(), blm);
+    if (blx) std::memcpy(hs + olx, P.xblocks.data(), blx);
+    if ((blg && (e = cudaMemcpyAsync(h->d_lgroups.p, hs + olg, blg, cudaMemcpyHostToDevice, stream)) != cudaSuccess) ||
+        (bli && (e = cudaMemcpyAsync(h->d_litems.p, hs + oli, bli, cudaMemcpyHostToDevice, stream)) != cudaSuccess) ||
+        (blm && (e = cudaMemcpyAsync(h->d_lmembers.p, hs + olm, blm, cudaMemcpyHostToDevice, stream)) != cudaSuccess) ||
+        (blx && (e = cudaMemcpyAsync(h->d_lxb.p, hs + olx, blx, cudaMemcpyHostToDevice, stream)) != cudaSuccess))
+        return h->cuda_fail(e, "lane table upload");
     if ((e = cudaMemcpyAsync(h->d_insts.p, hs, bi, cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
         (bt && (e = cudaMemcpyAsync(h->d_items.p, hs + bi, bt, cudaMemcpyHostToDevice, stream)) != cudaSuccess) ||
         (bg && (e = cudaMemcpyAsync(h->d_groups.p, hs + bi + bt, bg, cudaMemcpyHostToDevice, stream)) !=
@@ -745,6 +931,16 @@ te_status prepare_sweep(te_handle* h, const Plan& P, bool* grew) {
         (e = h->d_strip_k2.ensure((size_t)std::max<int64_t>(2, 2 * P.strip_total), grew)) != cudaSuccess)
         return h->fail(TE_ENOMEM, "sort scratch: %s", cudaGetErrorString(e));
     if ((e = te::prepare_sort_kernel(P.nmax)) != cudaSuccess) return h->cuda_fail(e, "sort kernel attribute");
+    if (!P.lgroups.empty()) {
+        if ((e = h->d_lgroups.ensure(P.lgroups.size(), grew)) != cudaSuccess ||
+            (e = h->d_litems.ensure(P.litems.size(), grew)) != cudaSuccess ||
+            (e = h->d_lmembers.ensure(P.lmembers.size(), grew)) != cudaSuccess ||
+            (e = h->d_tpart.ensure((size_t)P.tp_total, grew)) != cudaSuccess ||
+            (e = h->d_lrw.ensure((size_t)P.sorted_total, grew)) != cudaSuccess ||
+            (e = h->d_lxb.ensure(P.xblocks.size(), grew)) != cudaSuccess ||
+            (e = h->d_lx.ensure((size_t)P.x_total, grew)) != cudaSuccess)
+            return h->fail(TE_ENOMEM, "lane workspace: %s", cudaGetErrorString(e));
+    }
     return TE_OK;
 }
 
@@ -779,6 +975,15 @@ BatchArgs batch_args(te_handle* h, const Plan& P, int k, int32_t* counts, float*
         a.members = h->d_members.p;
         a.strip_pos = h->d_strip_pos.p;
         a.strip_k2 = h->d_strip_k2.p;
+        if (!P.lgroups.empty()) {
+            a.lgroups = h->d_lgroups.p;
+            a.litems = h->d_litems.p;
+            a.tpart = h->d_tpart.p;
+            a.lane_rw = h->d_lrw.p;
+            a.lane_members = h->d_lmembers.p;
+            a.lane_xb = h->d_lxb.p;
+            a.lane_x = h->d_lx.p;
+        }
     }
     return a;
 }
@@ -791,7 +996,7 @@ te_status run_per_instance(te_handle* h, const Plan& P, int n_inst, int k, doubl
     te_status st = upload_tables(h, P, stream);
     if (st != TE_OK) return st;
     h->drop_graph();
-    cudaError_t e = cudaMemsetAsync(h->d_words.p + 4, 0, (size_t)n_inst * sizeof(int32_t), stream);
+    cudaError_t e = cudaMemsetAsync(h->d_words.p + kWordPerInstance, 0, (size_t)n_inst * sizeof(int32_t), stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "clear queues");
     const BatchArgs a = batch_args(h, P, k, counts, eps);
     int launches = 0;
@@ -804,7 +1009,7 @@ te_status run_per_instance(te_handle* h, const Plan& P, int n_inst, int k, doubl
         BatchArgs ai = a;
         ai.item_base = I.item_begin;
         ai.n_items = I.n_items;
-        ai.queue = h->d_words.p + 4 + i;
+        ai.queue = h->d_words.p + kWordPerInstance + i;
         if (h->profiling && i == 0 && (e = cudaEventRecord(h->ev0, stream)) != cudaSuccess)
             return h->cuda_fail(e, "event");
         if ((e = te::launch_batched(P.var, ai, std::min(I.n_items, P.grid), P.threads, P.smem, stream)) !=
@@ -839,7 +1044,7 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
     cudaError_t e;
     if ((e = h->d_insts.ensure(P.insts.size(), &grew)) != cudaSuccess ||
         (e = h->d_items.ensure(P.items.size(), &grew)) != cudaSuccess ||
-        (e = h->d_words.ensure(4 + (size_t)n_inst, &grew)) != cudaSuccess ||
+        (e = h->d_words.ensure(kWordPerInstance + (size_t)n_inst, &grew)) != cudaSuccess ||
         (e = h->d_partial.ensure((size_t)P.n_parts, &grew)) != cudaSuccess ||
         (e = h->d_partial_abs.ensure((size_t)P.n_parts, &grew)) != cudaSuccess ||
         (n_groups > 0 && (e = h->d_te_all.ensure((size_t)n_inst, &grew)) != cudaSuccess))
@@ -849,6 +1054,13 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
     h->last_pairs = P.exhaustive_pairs;
     h->last_ops = P.exhaustive_ops;
     h->last_bundled = P.n_bundled;
+    {
+        int nb = 0;
+        for (const auto& I : P.insts) nb += I.bundle_n;
+        h->last_paths[0] = P.n_lane;
+        h->last_paths[1] = nb;
+        h->last_paths[2] = n_inst - P.n_lane - nb;
+    }
     if (grew) {
         ++h->workspace_gen;
         // a fresh flag word must start cleared
@@ -864,7 +1076,9 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
     const int cfg[] = {k, P.threads, P.grid, P.smem_floats, P.var.dlo, P.var.dhi, P.var.ks, P.var.qpt,
                        P.var.warp_only ? 1 : 0,
                        n_groups, S, h->profiling ? 1 : 0, n_inst, P.var.sweep ? 1 : 0, P.bd, P.bgrid,
-                       (int)P.bsmem, P.tgrid, (int)P.tsmem, P.n_bres};
+                       (int)P.bsmem, P.tgrid, (int)P.tsmem, P.n_bres, P.n_lane, P.lane_max_np,
+                       P.lane_grid[2], P.lane_grid[3], P.lane_grid[4], P.lane_grid[5], P.lane_grid[6],
+                       P.lane_grid[7], P.lane_grid[8]};
     key = fnv(key, cfg, sizeof cfg);
     const bool replay = !h->per_instance && h->graph_exec && h->graph_key == key &&
                         h->graph_gen == h->workspace_gen;
@@ -889,8 +1103,27 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
             ce = launch_sweep_prepass(h, P, h->cap_stream);
             ++launches;
         }
+        if (ce == cudaSuccess && !P.lgroups.empty()) {
+            ce = cudaMemsetAsync(h->d_words.p + kWordLaneQueue, 0, (kWordPerInstance - kWordLaneQueue) * sizeof(int32_t),
+                                 h->cap_stream);
+            if (ce == cudaSuccess)
+                ce = te::launch_lane_stage(h->d_lgroups.p, (int)P.lgroups.size(), P.lane_max_np, h->d_sidx.p,
+                                           h->d_tpart.p, h->d_lrw.p, h->d_lxb.p, (int)P.xblocks.size(), P.x_max,
+                                           h->d_lx.p, h->d_words.p + 1, h->cap_stream);
+            ++launches;
+        }
         // an event recorded during capture becomes a graph node only with cudaEventRecordExternal
         if (ce == cudaSuccess && h->profiling) ce = cudaEventRecordWithFlags(h->ev0, h->cap_stream, cudaEventRecordExternal);
+        for (int d = te::kLaneMinD; d <= te::kLaneMaxD && ce == cudaSuccess; ++d) {
+            const int n = P.lane_begin[d + 1] - P.lane_begin[d];
+            if (n <= 0) continue;
+            BatchArgs al = a;
+            al.item_base = P.lane_begin[d];
+            al.n_items = n;
+            al.queue = h->d_words.p + kWordLaneQueue + (d - te::kLaneMinD);
+            ce = te::launch_lanes(d, P.var.ks, al, P.lane_grid[d], h->cap_stream);
+            ++launches;
+        }
         for (int tiled = 0; tiled < 2 && ce == cudaSuccess; ++tiled) {
             const int n = tiled ? (int)P.bitems.size() - P.n_bres : P.n_bres;
             if (n <= 0) continue;
@@ -1011,6 +1244,13 @@ TE_EXPORT void te_destroy(te_handle* h) {
     h->d_exec.release();
     h->d_bitems.release();
     h->d_members.release();
+    h->d_lgroups.release();
+    h->d_litems.release();
+    h->d_lmembers.release();
+    h->d_lrw.release();
+    h->d_tpart.release();
+    h->d_lxb.release();
+    h->d_lx.release();
     h->h_stage.release();
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
@@ -1206,14 +1446,15 @@ TE_EXPORT te_status te_autotune(te_handle* h, const te_series* series, int32_t n
     DeviceGuard g(h->device);
     cudaStream_t strm = static_cast<cudaStream_t>(stream);
     const int save_t = h->cfg_threads, save_q = h->cfg_qpt;
-    const bool save_prof = h->profiling, save_share = h->sharing;
+    const bool save_prof = h->profiling;
+    const int save_share = h->sharing;
     auto restore = [&]() {
         h->cfg_threads = save_t;
         h->cfg_qpt = save_q;
         h->profiling = save_prof;
         h->sharing = save_share;
     };
-    h->sharing = false;  // the shapes tuned are those of the batched kernel
+    h->sharing = 0;  // the shapes tuned are those of the batched kernel
     h->cfg_threads = h->cfg_qpt = 0;
     Plan P;
     if ((st = build_plan(h, series, n_series, inst, n_inst, k, &P)) != TE_OK) {
@@ -1399,7 +1640,15 @@ TE_EXPORT te_status te_last_work(te_handle* h, uint64_t* pairs, uint64_t* ops, i
 
 TE_EXPORT te_status te_set_sharing(te_handle* h, int32_t enable) {
     if (!h) return TE_EINVAL;
-    h->sharing = enable != 0;
+    h->err.clear();
+    if (enable < 0 || enable > 2) return h->fail(TE_EINVAL, "te_set_sharing: %d is not 0, 1 or 2", enable);
+    h->sharing = enable;
+    return TE_OK;
+}
+
+TE_EXPORT te_status te_last_paths(te_handle* h, int32_t* paths) {
+    if (!h || !paths) return TE_EINVAL;
+    for (int i = 0; i < 3; ++i) paths[i] = h->last_paths[i];
     return TE_OK;
 }
 

@@ -73,6 +73,46 @@ constexpr int kBatchedMaxThreads = 512;
 // CTA of the warp-mode sweep kernel (d <= 2, every estimate resident in shared memory).
 constexpr int kSweepWarpThreads = 1024;
 
+// One estimate per lane (te_lanes.cuh): a group of estimates that share one target part (target
+// series, repetitions, window start, window, d, tau) and one sorted order. Its members are
+// members[mem_off .. mem_off + n_mem - 1] (instance indices), processed in blocks of 32 (one per
+// lane); its sorted target part is tpart[tp_off ..] ((d + 2) / 2 rows of NP = N rounded up to 32
+// float2) and the (repetition, sample) of each sorted position lane_rw[sort_off ..].
+struct LaneGroup {
+    const float* tgt;
+    int64_t sort_off;      // the group's sorted order (sorted_idx / sorted_key / lane_rw)
+    int64_t tp_off;        // its sorted target part
+    int32_t R, T, W, t_start, N, d, tau;
+    int32_t mem_off, n_mem;
+    int32_t reserved;
+};
+
+// Source part of a block of 32 estimates, member-minor (written by lane_x_kernel): for repetition
+// r, sample t = t0 + c and lane l, X[off + (r * ncols + c) * 32 + l] = src_l[perm_l[r]][t] (the lane's
+// source repetition paired with target repetition r; perm nullptr: the identity). One coalesced
+// 128-byte line then holds one source coordinate of one point for all 32 estimates (lanes past a
+// ragged group's last estimate repeat it). Blocks with
+// the same source series and pairings (the same surrogates at every analysis time point) share one
+// array; the columns cover every sample their groups read.
+struct LaneXBlock {
+    int64_t off;
+    int32_t R, T, t0, ncols;
+    const float* src[32];
+    const int32_t* perm[32];
+};
+
+// Work item of the lane kernel: sorted query positions q0 .. q0 + kLaneQB - 1 of group `group`
+// against its estimates mblock * 32 .. mblock * 32 + 31, whose source parts are X block xblk.
+struct LaneItem {
+    int32_t group, mblock, q0, xblk;
+};
+
+constexpr int kLaneWarps = 8;
+constexpr int kLaneThreads = 32 * kLaneWarps;
+constexpr int kLaneQB = 256;         // sorted query positions per work item (one partial sum each)
+constexpr int kLaneMinMembers = 8;   // smallest group the lane kernel takes
+constexpr int kLaneMinD = 2, kLaneMaxD = 8;
+
 // Bits of the device flag word.
 enum : int32_t { kFlagBadPerm = 1 };
 
@@ -97,6 +137,13 @@ struct BatchArgs {
     const int32_t* members;     // bundle kernel: member instance indices (leader first)
     const int32_t* strip_pos;   // sweep with strips: per group S + 1 sorted positions
     const float* strip_k2;      // sweep with strips: per group S (lowest, highest) y_t
+    const LaneGroup* lgroups;   // lane kernel: groups, work items, sorted target parts, (r, w)
+    const LaneItem* litems;
+    const float2* tpart;
+    const int32_t* lane_rw;
+    const int32_t* lane_members;
+    const LaneXBlock* lane_xb;
+    const float* lane_x;
 };
 
 // ---- launchers (te_unit.cu) ----
@@ -143,6 +190,14 @@ constexpr int kBundleQ = 1;         // queries per thread
 constexpr int kBundleThreads = 256;
 const void* bundle_kernel_ptr(int d, int ks, bool tiled);
 cudaError_t launch_bundle(int d, int ks, bool tiled, const BatchArgs& a, int grid, size_t smem, cudaStream_t s);
+// ---- the lane kernel (te_lanes_*.cu): one estimate per lane, d = kLaneMinD .. kLaneMaxD, k <= 4 ----
+const void* lane_kernel_ptr(int d, int ks);
+const void* lane_ptr_lo(int d, int ks);
+const void* lane_ptr_hi(int d, int ks);
+cudaError_t launch_lanes(int d, int ks, const BatchArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_lane_stage(const LaneGroup* groups, int n_groups, int max_np, const int32_t* sorted_idx,
+                              float2* tpart, int32_t* lane_rw, const LaneXBlock* xblocks, int n_xblocks,
+                              int64_t max_x, float* lane_x, int32_t* flags, cudaStream_t s);
 cudaError_t launch_finalize_te(const InstDesc* insts, int n_inst, const double* partial,
                                const double* partial_abs, double psi_k, double err_coef,
                                double* te, double* err, cudaStream_t s);

@@ -29,7 +29,8 @@ EXPORTS = ["te_create", "te_destroy", "te_last_error", "te_sync_status", "te_emb
            "te_knn_maxnorm", "te_range_count", "te_estimate", "te_surrogate_test",
            "te_set_profiling", "te_last_kernel_ms", "te_last_launch_count", "te_set_launch_config",
            "te_set_batching", "te_surrogate_test_static", "te_autotune", "te_delay_scan",
-           "te_set_search", "te_last_work", "te_set_sharing", "te_last_alu_ops", "te_last_pass_work"]
+           "te_set_search", "te_last_work", "te_set_sharing", "te_last_alu_ops", "te_last_pass_work",
+           "te_last_paths"]
 
 
 class TEError(RuntimeError):
@@ -95,13 +96,15 @@ def load() -> C.CDLL:
     lib.te_set_sharing.argtypes = [P, i32]
     lib.te_last_alu_ops.argtypes = [P, C.POINTER(C.c_uint64), C.POINTER(i32)]
     lib.te_last_pass_work.argtypes = [P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
+    lib.te_last_paths.argtypes = [P, C.POINTER(i32)]
     lib.te_delay_scan.argtypes = [P, C.POINTER(te_series), P, i32, i32, i32, i32, i32, i32, P, P, P, P]
     lib.te_autotune.argtypes = [P, C.POINTER(te_series), i32, C.POINTER(te_instance), i32, i32,
                                 C.c_char_p, C.POINTER(i32), C.POINTER(i32), P]
     for name in ("te_sync_status", "te_embed", "te_knn_maxnorm", "te_range_count", "te_estimate",
                  "te_surrogate_test", "te_set_profiling", "te_last_kernel_ms",
                  "te_last_launch_count", "te_set_launch_config", "te_set_batching", "te_autotune", "te_delay_scan",
-                 "te_set_search", "te_last_work", "te_set_sharing", "te_last_alu_ops", "te_last_pass_work"):
+                 "te_set_search", "te_last_work", "te_set_sharing", "te_last_alu_ops", "te_last_pass_work",
+                 "te_last_paths"):
         getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -413,9 +416,21 @@ def te_last_work(h: Handle):
     return int(pr.value), int(op.value), bool(sw.value)
 
 
-def te_set_sharing(h: Handle, enable: bool):
-    """True (default): estimates with one target part run in bundles that compute it once."""
-    h.check(h.lib.te_set_sharing(h.h, 1 if enable else 0))
+SHARE_NONE, SHARE_AUTO, SHARE_BUNDLES = 0, 1, 2
+
+
+def te_set_sharing(h: Handle, mode):
+    """Target-part sharing: 1 or True (default) = one estimate per lane for groups of at least 8
+    estimates with one target part and d = 2..8, bundles of up to 3 for smaller groups; 2 =
+    bundles only; 0 or False = none."""
+    h.check(h.lib.te_set_sharing(h.h, int(mode)))
+
+
+def te_last_paths(h: Handle):
+    """(estimates on the lane kernel, in bundles, unshared) of the last batched call."""
+    v = (C.c_int32 * 3)()
+    h.check(h.lib.te_last_paths(h.h, v))
+    return int(v[0]), int(v[1]), int(v[2])
 
 
 def te_last_pass_work(h: Handle):

@@ -170,7 +170,9 @@ def test_deterministic_and_graph_replay(te_handle):
     c = te.te_estimate(te_handle, ds, w.instances, w.k)                  # new output: re-capture
     torch.cuda.synchronize()
     swept = te.te_last_work(te_handle)[2]
-    assert n1 == 2 + int(swept)  # persistent kernel + finalisation (+ the sweep's sort pre-pass)
+    lanes = te.te_last_paths(te_handle)[0] > 0
+    # persistent kernel + finalisation (+ the sweep's sort pre-pass, + the lane kernel's pre-pass)
+    assert n1 == 2 + int(swept) + int(lanes)
     assert torch.equal(a, b) and torch.equal(a, c)
 
 
@@ -183,7 +185,8 @@ def test_profiling_hook_and_launch_count(te_handle):
         ms = te.te_last_kernel_ms(te_handle)
         assert ms > 0
         swept = te.te_last_work(te_handle)[2]
-        assert te.te_last_launch_count(te_handle) == 3 + int(swept)
+        lanes = te.te_last_paths(te_handle)[0] > 0
+        assert te.te_last_launch_count(te_handle) == 3 + int(swept) + int(lanes)
     finally:
         te.te_set_profiling(te_handle, False)
 
@@ -261,13 +264,13 @@ def test_per_instance_launch_mode_is_bit_identical(te_handle):
 
 
 def test_per_instance_launch_mode_with_resident_and_shared_estimates(te_handle):
-    # C3 shapes: in one launch the estimates are staged whole and bundled by target part; per
+    # C3 shapes: in one launch the estimates share their target part (one estimate per lane); per
     # instance they run the tiled search without sharing, so the partial sums are grouped
     # differently: counts and eps stay bit-identical, TE agrees within the error bound
     w = I.config(3, n_t=2, S=20)
     ds = te.to_device(w.series)
     ref = te.te_estimate(te_handle, ds, w.instances, w.k, want_err=True, want_counts=True)
-    assert te.te_last_alu_ops(te_handle)[1] > 0
+    assert te.te_last_paths(te_handle)[0] == len(w.instances)
     te.te_set_batching(te_handle, True)
     try:
         got = te.te_estimate(te_handle, ds, w.instances, w.k, want_err=True, want_counts=True)

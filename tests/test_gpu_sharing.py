@@ -3,7 +3,9 @@ trial-shuffled surrogates, every scanned delay u) run in bundles that compute th
 each distance and count once. Per-point radii and counts must equal the unshared search and the
 CPU oracle bit for bit, TE within 1e-6 nats of the oracle; bundles of every size 2..3, ragged
 point counts, mixed embedding dimensions, the delay scan and a bad permutation entry.
-Bundles hold up to 3 estimates (never 1: a remainder of one turns the last two bundles into 2 + 2)."""
+Bundles hold up to 3 estimates (never 1: a remainder of one turns the last two bundles into 2 + 2).
+Groups of 8 or more estimates with d >= 2 go to the lane kernel by default (tests/test_gpu_lanes.py);
+the tests here ask for bundles only (te.SHARE_BUNDLES) where their groups are that large."""
 import numpy as np
 import pytest
 import torch
@@ -17,7 +19,7 @@ TOL = 1e-6
 
 
 def _estimate(h, ds, insts, k, sharing):
-    te.te_set_sharing(h, sharing)
+    te.te_set_sharing(h, te.SHARE_BUNDLES if sharing is True else sharing)
     try:
         res = te.te_estimate(h, ds, insts, k, want_err=True, want_counts=True)
         torch.cuda.synchronize()
@@ -154,11 +156,12 @@ def test_delay_scan_with_tiled_bundles(te_handle):
     try:
         off = te.te_delay_scan(te_handle, ds[0], starts, w.window, 44, 46, w.S, w.k)
         torch.cuda.synchronize()
+        te.te_set_sharing(te_handle, te.SHARE_BUNDLES)
+        on = te.te_delay_scan(te_handle, ds[0], starts, w.window, 44, 46, w.S, w.k)
+        torch.cuda.synchronize()
+        assert te.te_last_alu_ops(te_handle)[1] == 3  # 3 delays x 3 estimates = 9
     finally:
         te.te_set_sharing(te_handle, True)
-    on = te.te_delay_scan(te_handle, ds[0], starts, w.window, 44, 46, w.S, w.k)
-    torch.cuda.synchronize()
-    assert te.te_last_alu_ops(te_handle)[1] == 3  # 3 delays x 3 estimates = 9
     assert torch.max(torch.abs(off["te"] - on["te"])).item() <= 1e-12
     assert torch.equal(off["p"], on["p"]) and torch.equal(off["u_best"], on["u_best"])
     wa = I.ar1_analysis("unidirectional", S=4, R=50, window=300, n_windows=1)
