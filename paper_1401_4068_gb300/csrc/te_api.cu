@@ -132,6 +132,7 @@ struct Plan {
     std::vector<te::LaneItem> litems;
     std::vector<int32_t> lmembers;
     int64_t tp_total = 0;          // float2 entries of the sorted target parts
+    int64_t rw_total = 0;          // entries of the (repetition, sample) tables
     std::vector<te::LaneXBlock> xblocks;
     int64_t x_total = 0, x_max = 0;  // floats of all / the largest member-minor source array
     int lane_max_np = 0;
@@ -528,7 +529,8 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
             xtotal += n;
             xmax = std::max(xmax, n);
         }
-        if (xtotal * (int64_t)sizeof(float) > kLaneXMaxBytes) cand.clear();
+        // the kernel indexes one array with 32-bit offsets
+        if (xtotal * (int64_t)sizeof(float) > kLaneXMaxBytes || xmax >= ((int64_t)1 << 31)) cand.clear();
         for (size_t g = 0; g < cand.size(); ++g) {
             const std::vector<int>& v = cand[g];
             const InstDesc& I0 = P->insts[v[0]];
@@ -546,6 +548,8 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
             const int NP = (I0.N + 31) & ~31;
             G.tp_off = P->tp_total;
             P->tp_total += (int64_t)((I0.d + 2) / 2) * NP;
+            G.rw_off = P->rw_total;
+            P->rw_total += NP;
             P->lane_max_np = std::max(P->lane_max_np, NP);
             const int nqb = (I0.N + te::kLaneQB - 1) / te::kLaneQB;
             for (int i : v) {
@@ -936,7 +940,7 @@ te_status prepare_sweep(te_handle* h, const Plan& P, bool* grew) {
             (e = h->d_litems.ensure(P.litems.size(), grew)) != cudaSuccess ||
             (e = h->d_lmembers.ensure(P.lmembers.size(), grew)) != cudaSuccess ||
             (e = h->d_tpart.ensure((size_t)P.tp_total, grew)) != cudaSuccess ||
-            (e = h->d_lrw.ensure((size_t)P.sorted_total, grew)) != cudaSuccess ||
+            (e = h->d_lrw.ensure((size_t)P.rw_total, grew)) != cudaSuccess ||
             (e = h->d_lxb.ensure(P.xblocks.size(), grew)) != cudaSuccess ||
             (e = h->d_lx.ensure((size_t)P.x_total, grew)) != cudaSuccess)
             return h->fail(TE_ENOMEM, "lane workspace: %s", cudaGetErrorString(e));

@@ -76,12 +76,14 @@ constexpr int kSweepWarpThreads = 1024;
 // One estimate per lane (te_lanes.cuh): a group of estimates that share one target part (target
 // series, repetitions, window start, window, d, tau) and one sorted order. Its members are
 // members[mem_off .. mem_off + n_mem - 1] (instance indices), processed in blocks of 32 (one per
-// lane); its sorted target part is tpart[tp_off ..] ((d + 2) / 2 rows of NP = N rounded up to 32
-// float2) and the (repetition, sample) of each sorted position lane_rw[sort_off ..].
+// lane); its sorted target part is tpart[tp_off ..] ((d + 2) / 2 float2 per position, chunk-major
+// in chunks of 32 positions, N rounded up to 32) and the (repetition, sample) of each sorted
+// position lane_rw[rw_off ..] (N rounded up to 32 entries).
 struct LaneGroup {
     const float* tgt;
-    int64_t sort_off;      // the group's sorted order (sorted_idx / sorted_key / lane_rw)
+    int64_t sort_off;      // the group's sorted order (sorted_idx)
     int64_t tp_off;        // its sorted target part
+    int64_t rw_off;        // its (repetition, sample) table
     int32_t R, T, W, t_start, N, d, tau;
     int32_t mem_off, n_mem;
     int32_t reserved;

@@ -40,18 +40,23 @@ __device__ __forceinline__ u64 pack2(float lo, float hi) {
     return r;
 }
 
-// Source coordinates x_{t-u}, x_{t-u-tau}, ... of point (r, t) for the lane's estimate (delay u),
-// read from the block's member-minor array (LaneXBlock) as packed pairs for sub.rn.f32x2 (an odd d
-// repeats its last coordinate: max is unchanged); one 128-byte line per coordinate for the warp.
+// Source coordinates x_{t-u}, x_{t-u-tau}, ... of one point for the lane's estimate, read from the
+// block's member-minor array (LaneXBlock) at xp (the point's column) as packed pairs for
+// sub.rn.f32x2 (an odd d repeats its last coordinate: max is unchanged); one 128-byte line per
+// coordinate for the warp.
 template <int d>
-__device__ __forceinline__ void lane_source(const float* __restrict__ xl, int ncols, int tau32, int r, int c,
-                                            u64 (&x2)[(d + 1) / 2]) {
-    const float* xp = xl + ((size_t)r * ncols + c) * 32;
+__device__ __forceinline__ void lane_source(const float* __restrict__ xp, int tau32, u64 (&x2)[(d + 1) / 2]) {
     float x[d];
 #pragma unroll
     for (int k = 0; k < d; ++k) x[k] = __ldg(xp - k * tau32);
 #pragma unroll
     for (int c2 = 0; c2 < (d + 1) / 2; ++c2) x2[c2] = pack2(x[2 * c2], x[2 * c2 + 1 < d ? 2 * c2 + 1 : 2 * c2]);
+}
+
+// offset (floats, relative to the lane's column base) of point rw = r << 16 | w in a member-minor
+// array of ncols32 = 32 * columns floats per repetition
+__device__ __forceinline__ int lane_xoff(uint32_t rw, int ncols32) {
+    return (int)(rw >> 16) * ncols32 + (int)(rw & 0xffffu) * 32;
 }
 
 // max(a, |q_c - x_c| over the d source coordinates), a >= 0
@@ -65,143 +70,244 @@ __device__ __forceinline__ float lane_join(float a, const u64 (&q2)[(d + 1) / 2]
     return absmax_range<0, 2 * P>(v);
 }
 
-// Sorted target part of a lane group's points (written by lane_stage_kernel): DA2 rows of NP
-// float2, row c2 holding coordinates (2 c2, 2 c2 + 1) of the joint point (y_t, y_{t'-1},
-// y_{t'-1-tau}, ...), the last pair of an even d completed with coordinate 1 again; positions N ..
-// NP-1 hold +inf. rw[p] = r << 16 | w of the point at sorted position p (N <= 65536, so r, w <
-// 65536).
+// Sorted target part of a lane group (written by lane_stage_kernel), chunk-major: chunk ch (sorted
+// positions 32 ch .. 32 ch + 31) holds DA2 = (d + 2) / 2 rows of 32 float2, row c2 the coordinates
+// (2 c2, 2 c2 + 1) of the joint point (y_t, y_{t'-1}, y_{t'-1-tau}, ...), the last pair of an even
+// d completed with coordinate 1 again; positions past N hold +inf. So a chunk's loads are one
+// pointer plus constant offsets, and the key y_{t'-1} of its first and last position are .y of its
+// row-0 entries 0 and 31. rw[32 ch + l] = r << 16 | w of the point at sorted position 32 ch + l
+// (0 past N).
 template <int d>
-__device__ __forceinline__ void lane_target(const float2* __restrict__ tp, int NP, int j, u64 (&r2)[(d + 2) / 2]) {
+__device__ __forceinline__ void lane_load(const float2* __restrict__ cp, const int32_t* __restrict__ rwp,
+                                          float2 (&r)[(d + 2) / 2], int32_t& rw) {
 #pragma unroll
-    for (int c2 = 0; c2 < (d + 2) / 2; ++c2) {
-        const float2 v = __ldg(tp + (size_t)c2 * NP + j);
-        r2[c2] = pack2(v.x, v.y);
+    for (int c2 = 0; c2 < (d + 2) / 2; ++c2) r[c2] = __ldg(cp + c2 * 32);
+    rw = __ldg(rwp);
+}
+
+template <int d>
+__device__ __forceinline__ void lane_diff(const float2 (&r)[(d + 2) / 2], const u64 (&tq)[(d + 2) / 2],
+                                          float (&v)[2 * ((d + 2) / 2)]) {
+#pragma unroll
+    for (int c2 = 0; c2 < (d + 2) / 2; ++c2) split2(sub2(tq[c2], pack2(r[c2].x, r[c2].y)), v[2 * c2], v[2 * c2 + 1]);
+}
+
+// Passing references evaluated per round of a lane sweep (their loads in flight together), chosen
+// per embedding dimension by measurement on GB300: 4 for d <= 3 (C3 shapes), an explicitly
+// written pair (0) for d = 4 (the Lorenz delay scan), 2 for d >= 5 (C5 shapes).
+template <int d>
+__host__ __device__ constexpr int lane_round() { return d <= 3 ? 4 : (d == 4 ? 0 : 2); }
+
+// pass 1: push the joint distances of the references in `ball` (their dT and source offsets xo
+// live in the lanes named by the bits) into the lane's top-k list
+template <int d, int KS, int RB>
+__device__ __forceinline__ void lane_push_refs(unsigned ball, float dT, int xo, const float* __restrict__ xlq, int tau32,
+                                               const u64 (&xq)[(d + 1) / 2], float (&t)[KS]) {
+    constexpr int P = (d + 1) / 2;
+    if constexpr (RB == 0) {
+        while (ball) {
+            const int j0 = __ffs(ball) - 1;
+            ball &= ball - 1;
+            const bool two = ball != 0;
+            const int j1 = two ? __ffs(ball) - 1 : j0;
+            if (two) ball &= ball - 1;
+            const float dT0 = __shfl_sync(0xffffffffu, dT, j0);
+            const float dT1 = __shfl_sync(0xffffffffu, dT, j1);
+            const int xo0 = __shfl_sync(0xffffffffu, xo, j0);
+            const int xo1 = __shfl_sync(0xffffffffu, xo, j1);
+            u64 x0[P], x1[P];
+            lane_source<d>(xlq + xo0, tau32, x0);
+            lane_source<d>(xlq + xo1, tau32, x1);
+            const float d0 = lane_join<d>(dT0, xq, x0);
+            const float d1 = two ? lane_join<d>(dT1, xq, x1) : f_inf();
+            topk_push(t, d0);
+            topk_push(t, d1);
+        }
+    } else {
+        while (ball) {
+            int jr[RB];
+            bool ok[RB];
+#pragma unroll
+            for (int b = 0; b < RB; ++b) {
+                ok[b] = ball != 0;
+                jr[b] = ok[b] ? __ffs(ball) - 1 : jr[0];
+                ball &= ball - 1;
+            }
+            u64 xr[RB][P];
+            float dr[RB];
+#pragma unroll
+            for (int b = 0; b < RB; ++b) {
+                dr[b] = __shfl_sync(0xffffffffu, dT, jr[b]);
+                lane_source<d>(xlq + __shfl_sync(0xffffffffu, xo, jr[b]), tau32, xr[b]);
+            }
+#pragma unroll
+            for (int b = 0; b < RB; ++b)  // a missing reference pushes +inf (no change)
+                topk_push(t, ok[b] ? lane_join<d>(dr[b], xq, xr[b]) : f_inf());
+        }
+    }
+}
+
+// pass 2: count the references in `ball` (b = max |dy-| and |dy_t| in the lanes named by the bits)
+// against the lane's eps e
+template <int d, int RB>
+__device__ __forceinline__ void lane_count_refs(unsigned ball, float bv, float ay, int xo, const float* __restrict__ xlq,
+                                                int tau32, const u64 (&xq)[(d + 1) / 2], float e, float& cz,
+                                                float& cyz, float& cxz) {
+    constexpr int P = (d + 1) / 2;
+    if constexpr (RB == 0) {
+        const float ayz = fmaxf(ay, bv);  // (y_t, y-)
+        while (ball) {
+            const int j0 = __ffs(ball) - 1;
+            ball &= ball - 1;
+            const bool two = ball != 0;
+            const int j1 = two ? __ffs(ball) - 1 : j0;
+            if (two) ball &= ball - 1;
+            // a round with one reference left pairs it with +inf (counted nowhere)
+            const float b0 = __shfl_sync(0xffffffffu, bv, j0), y0 = __shfl_sync(0xffffffffu, ayz, j0);
+            float b1 = __shfl_sync(0xffffffffu, bv, j1), y1 = __shfl_sync(0xffffffffu, ayz, j1);
+            if (!two) b1 = y1 = f_inf();
+            const int xo0 = __shfl_sync(0xffffffffu, xo, j0);
+            const int xo1 = __shfl_sync(0xffffffffu, xo, j1);
+            u64 x0[P], x1[P];
+            lane_source<d>(xlq + xo0, tau32, x0);
+            lane_source<d>(xlq + xo1, tau32, x1);
+            const float x0m = lane_join<d>(b0, xq, x0);  // max(b, |dx-|)
+            const float x1m = lane_join<d>(b1, xq, x1);
+            cz += set_lt(b0, e) + set_lt(b1, e);
+            cyz += set_lt(y0, e) + set_lt(y1, e);
+            cxz += set_lt(x0m, e) + set_lt(x1m, e);
+        }
+    } else {
+        while (ball) {
+            int jr[RB];
+            bool ok[RB];
+#pragma unroll
+            for (int b = 0; b < RB; ++b) {
+                ok[b] = ball != 0;
+                jr[b] = ok[b] ? __ffs(ball) - 1 : jr[0];
+                ball &= ball - 1;
+            }
+            u64 xr[RB][P];
+            float br[RB], yr[RB];
+#pragma unroll
+            for (int b = 0; b < RB; ++b) {
+                // a missing reference gets b = +inf (counted nowhere)
+                br[b] = ok[b] ? __shfl_sync(0xffffffffu, bv, jr[b]) : f_inf();
+                yr[b] = __shfl_sync(0xffffffffu, ay, jr[b]);
+                lane_source<d>(xlq + __shfl_sync(0xffffffffu, xo, jr[b]), tau32, xr[b]);
+            }
+#pragma unroll
+            for (int b = 0; b < RB; ++b) {
+                cz += set_lt(br[b], e);
+                cyz += set_lt(fmaxf(yr[b], br[b]), e);
+                cxz += set_lt(lane_join<d>(br[b], xq, xr[b]), e);  // max(b, |dx-|)
+            }
+        }
     }
 }
 
 template <int d, int KS>
-__device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& G, const float* __restrict__ xl,
-                                           int ncols, int cu, bool mv, unsigned nv, int p, FF& acc, float& acc_abs,
+__device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& G, const float* __restrict__ xlq,
+                                           int ncols32, bool mv, unsigned nv, int p, FF& acc, float& acc_abs,
                                            const int64_t pt_off) {
     constexpr int DA2 = (d + 2) / 2;  // pairs of target coordinates (1 + d of them)
     constexpr int P = (d + 1) / 2;    // pairs of source coordinates
+    constexpr int CH = DA2 * 32;      // float2 per chunk
     const int lane = threadIdx.x & 31;
-    const int N = G.N, NP = (G.N + 31) & ~31;
-    const float2* tp = a.tpart + G.tp_off;
-    const int32_t* rwp = a.lane_rw + G.sort_off;
-    const float* skey = a.sorted_key + G.sort_off;
-
-    // the query (uniform): target coordinates, its repetition and sample; the lane's source part
-    u64 tq[DA2];
-    lane_target<d>(tp, NP, p, tq);
-    const uint32_t rwq = (uint32_t)__ldg(rwp + p);
-    // column of the source sample x_{t-u} of a point at window offset w: cu + w (cu = t_start - u - t0)
+    const int N = G.N, nch = (G.N + 31) >> 5;
+    const float2* tpb = a.tpart + G.tp_off;  // uniform base; tpb + lane: this lane's column
+    const float2* tpl = tpb + lane;
+    const int32_t* rwl = a.lane_rw + G.rw_off + lane;
     const int tau32 = G.tau * 32;
-    u64 xq[P];
-    lane_source<d>(xl, ncols, tau32, (int)(rwq >> 16), cu + (int)(rwq & 0xffffu), xq);
+
+    // the query (uniform): target coordinates and key; the lane's source part
+    const int pc = p >> 5;
+    u64 tq[DA2];
+#pragma unroll
+    for (int c2 = 0; c2 < DA2; ++c2) {
+        const float2 q = __ldg(tpb + pc * CH + c2 * 32 + (p & 31));
+        tq[c2] = pack2(q.x, q.y);
+    }
     float keyq, tmp;
     split2(tq[0], tmp, keyq);
+    u64 xq[P];
+    lane_source<d>(xlq + lane_xoff((uint32_t)__ldg(a.lane_rw + G.rw_off + p), ncols32), tau32, xq);
 
     pass1_begin(a);
-    unsigned long long visited = 0, passed = 0;
+    unsigned vis1 = 0, pas1 = 0;
     float t[KS];
 #pragma unroll
     for (int s = 0; s < KS; ++s) t[s] = f_inf();
     float thr = f_inf();
-    const int cb = p & ~31;
-    int cl = cb, cr = cb;
-    // one chunk of 32 sorted positions (one reference per lane)
-    auto chunk1 = [&](int c) {
-        const int j = c + lane;
-        u64 r2[DA2];
-        lane_target<d>(tp, NP, j, r2);
+    int chl = pc, chr = pc;
+    // one chunk (a reference per lane; its data r, rw already loaded): the target-part distance dT,
+    // then every reference with dT < thr for all lanes, two per round (independent loads)
+    auto scan1 = [&](const float2 (&r)[DA2], int32_t rwv, int ch) {
         float v[2 * DA2];
-#pragma unroll
-        for (int c2 = 0; c2 < DA2; ++c2) split2(sub2(tq[c2], r2[c2]), v[2 * c2], v[2 * c2 + 1]);
+        lane_diff<d>(r, tq, v);
         const float dT = absmax_range<0, 2 * DA2 - 1>(v);
         unsigned ball = __ballot_sync(0xffffffffu, dT < thr);
-        visited += (unsigned long long)min(32, N - c);
+        vis1 += min(32, N - (ch << 5));
         if (ball) {
-            const int rw = __ldg(rwp + min(j, N - 1));
-            passed += __popc(ball);
-            while (ball) {  // two passing references per round for independent loads
-                const int j0 = __ffs(ball) - 1;
-                ball &= ball - 1;
-                const bool two = ball != 0;
-                const int j1 = two ? __ffs(ball) - 1 : j0;
-                if (two) ball &= ball - 1;
-                const float dT0 = __shfl_sync(0xffffffffu, dT, j0);
-                const float dT1 = __shfl_sync(0xffffffffu, dT, j1);
-                const uint32_t rw0 = (uint32_t)__shfl_sync(0xffffffffu, rw, j0);
-                const uint32_t rw1 = (uint32_t)__shfl_sync(0xffffffffu, rw, j1);
-                u64 x0[P], x1[P];
-                lane_source<d>(xl, ncols, tau32, (int)(rw0 >> 16), cu + (int)(rw0 & 0xffffu), x0);
-                lane_source<d>(xl, ncols, tau32, (int)(rw1 >> 16), cu + (int)(rw1 & 0xffffu), x1);
-                const float d0 = lane_join<d>(dT0, xq, x0);
-                const float d1 = two ? lane_join<d>(dT1, xq, x1) : f_inf();
-                topk_push(t, d0);
-                topk_push(t, d1);
-            }
+            const int xo = lane_xoff((uint32_t)rwv, ncols32);
+            pas1 += __popc(ball);
+            lane_push_refs<d, KS, lane_round<d>()>(ball, dT, xo, xlq, tau32, xq, t);
         }
         thr = lanes_max(mv ? t[KS - 1] : 0.0f);
     };
-    chunk1(cb);
-    for (int c = cb + 32; c < N; c += 32) {  // right
-        if (!(__ldg(skey + c) < __fadd_ru(keyq, thr))) break;
-        chunk1(c);
-        cr = c;
+    // The sweeps load chunk ch + 1 (or ch - 1) before processing chunk ch, so its latency overlaps
+    // the work on ch; the window test reads the key of a chunk's first (right) or last (left)
+    // position from its loaded row 0. A prefetched chunk past the window is not used.
+    float2 cur[DA2], nxt[DA2];
+    int32_t rwc, rwn;
+    lane_load<d>(tpl + pc * CH, rwl + (pc << 5), cur, rwc);
+    if (pc + 1 < nch) lane_load<d>(tpl + (pc + 1) * CH, rwl + ((pc + 1) << 5), nxt, rwn);
+    scan1(cur, rwc, pc);
+    for (int ch = pc + 1; ch < nch; ++ch) {  // right: stop at the first chunk starting outside
+#pragma unroll
+        for (int c2 = 0; c2 < DA2; ++c2) cur[c2] = nxt[c2];
+        rwc = rwn;
+        if (!(__shfl_sync(0xffffffffu, cur[0].y, 0) < __fadd_ru(keyq, thr))) break;
+        if (ch + 1 < nch) lane_load<d>(tpl + (ch + 1) * CH, rwl + ((ch + 1) << 5), nxt, rwn);
+        scan1(cur, rwc, ch);
+        chr = ch;
     }
-    for (int c = cb - 32; c >= 0; c -= 32) {  // left
-        if (!(__ldg(skey + c + 31) > __fsub_rd(keyq, thr))) break;
-        chunk1(c);
-        cl = c;
+    if (pc > 0) lane_load<d>(tpl + (pc - 1) * CH, rwl + ((pc - 1) << 5), nxt, rwn);
+    for (int ch = pc - 1; ch >= 0; --ch) {  // left: stop at the first chunk ending outside
+#pragma unroll
+        for (int c2 = 0; c2 < DA2; ++c2) cur[c2] = nxt[c2];
+        rwc = rwn;
+        if (!(__shfl_sync(0xffffffffu, cur[0].y, 31) > __fsub_rd(keyq, thr))) break;
+        if (ch > 0) lane_load<d>(tpl + (ch - 1) * CH, rwl + ((ch - 1) << 5), nxt, rwn);
+        scan1(cur, rwc, ch);
+        chl = ch;
     }
     const float e = topk_select(t, a.k);
     const float emax = lanes_max(mv ? e : 0.0f);
-    pass1_end(a, visited * nv);
-    const unsigned long long visited1 = visited, passed1 = passed;
-    visited = passed = 0;
+    pass1_end(a, (unsigned long long)vis1 * nv);
 
-    // ---- pass 2: chunks of the window of the largest eps
+    // ---- pass 2: chunks of the window of the largest eps (inside those pass 1 visited)
     const float lb = __fsub_rd(keyq, emax), rb = __fadd_ru(keyq, emax);
     float cz = 0.0f, cyz = 0.0f, cxz = 0.0f;
-    for (int c = cl; c <= cr; c += 32) {
-        if (!(__ldg(skey + min(c + 31, N - 1)) > lb)) continue;
-        if (!(__ldg(skey + c) < rb)) break;
-        const int j = c + lane;
-        u64 r2[DA2];
-        lane_target<d>(tp, NP, j, r2);
-        float v[2 * DA2];
+    unsigned vis2 = 0, pas2 = 0;
+    lane_load<d>(tpl + chl * CH, rwl + (chl << 5), nxt, rwn);
+    for (int ch = chl; ch <= chr; ++ch) {
 #pragma unroll
-        for (int c2 = 0; c2 < DA2; ++c2) split2(sub2(tq[c2], r2[c2]), v[2 * c2], v[2 * c2 + 1]);
-        const float b = absmax_range<1, 2 * DA2 - 1>(v);   // y- (and the repeated coordinate 1)
-        const float ayz = fmaxf(fabsf(v[0]), b);           // (y_t, y-)
-        unsigned ball = __ballot_sync(0xffffffffu, b < emax);
-        visited += (unsigned long long)min(32, N - c);
+        for (int c2 = 0; c2 < DA2; ++c2) cur[c2] = nxt[c2];
+        rwc = rwn;
+        if (!(__shfl_sync(0xffffffffu, cur[0].y, 0) < rb)) break;
+        if (ch < chr) lane_load<d>(tpl + (ch + 1) * CH, rwl + ((ch + 1) << 5), nxt, rwn);
+        if (!(__shfl_sync(0xffffffffu, cur[0].y, 31) > lb)) continue;  // padding (+inf) never skips
+        float v[2 * DA2];
+        lane_diff<d>(cur, tq, v);
+        const float bv = absmax_range<1, 2 * DA2 - 1>(v);  // y- (and the repeated coordinate 1)
+        const float ayz = fabsf(v[0]);                     // y_t (joined with b per reference)
+        unsigned ball = __ballot_sync(0xffffffffu, bv < emax);
+        vis2 += min(32, N - (ch << 5));
         if (ball) {
-            const int rw = __ldg(rwp + min(j, N - 1));
-            passed += __popc(ball);
-            while (ball) {
-                const int j0 = __ffs(ball) - 1;
-                ball &= ball - 1;
-                const bool two = ball != 0;
-                const int j1 = two ? __ffs(ball) - 1 : j0;
-                if (two) ball &= ball - 1;
-                // a round with one reference left pairs it with +inf (counted nowhere)
-                const float b0 = __shfl_sync(0xffffffffu, b, j0), y0 = __shfl_sync(0xffffffffu, ayz, j0);
-                float b1 = __shfl_sync(0xffffffffu, b, j1), y1 = __shfl_sync(0xffffffffu, ayz, j1);
-                if (!two) b1 = y1 = f_inf();
-                const uint32_t rw0 = (uint32_t)__shfl_sync(0xffffffffu, rw, j0);
-                const uint32_t rw1 = (uint32_t)__shfl_sync(0xffffffffu, rw, j1);
-                u64 x0[P], x1[P];
-                lane_source<d>(xl, ncols, tau32, (int)(rw0 >> 16), cu + (int)(rw0 & 0xffffu), x0);
-                lane_source<d>(xl, ncols, tau32, (int)(rw1 >> 16), cu + (int)(rw1 & 0xffffu), x1);
-                const float x0m = lane_join<d>(b0, xq, x0);  // max(b, |dx-|)
-                const float x1m = lane_join<d>(b1, xq, x1);
-                cz += set_lt(b0, e) + set_lt(b1, e);
-                cyz += set_lt(y0, e) + set_lt(y1, e);
-                cxz += set_lt(x0m, e) + set_lt(x1m, e);
-            }
+            const int xo = lane_xoff((uint32_t)rwc, ncols32);
+            pas2 += __popc(ball);
+            lane_count_refs<d, lane_round<d>()>(ball, bv, ayz, xo, xlq, tau32, xq, e, cz, cyz, cxz);
         }
     }
     pass2_end(a);
@@ -233,9 +339,10 @@ __device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& 
         // ops) runs once per reference for all lanes, the source part (2 d) only for references
         // that passed the shared test
         constexpr int D = 1 + 2 * d;
-        const unsigned long long pairs = (visited1 + visited) * nv;
+        const unsigned long long vis = (unsigned long long)vis1 + vis2, pas = (unsigned long long)pas1 + pas2;
+        const unsigned long long pairs = vis * nv;
         const unsigned long long alg = pairs * 2ull * D;
-        const unsigned long long run = (visited1 + visited) * 2ull * (1 + d) + (passed1 + passed) * nv * 2ull * d;
+        const unsigned long long run = vis * 2ull * (1 + d) + pas * nv * 2ull * d;
         work_add(0, pairs);
         work_add(1, alg);
         work_add(2, alg > run ? alg - run : 0ull);
@@ -247,7 +354,7 @@ __device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& 
 // + kLaneWarps, ... (a fixed assignment, so the partial sums are deterministic), and the CTA adds
 // its warps' per-lane sums in warp order into one partial per estimate and query block.
 template <int d, int KS>
-__global__ void __launch_bounds__(kLaneThreads, d <= 5 ? 4 : 3) lane_kernel(const BatchArgs a) {
+__global__ void __launch_bounds__(kLaneThreads, d <= 4 ? 4 : 3) lane_kernel(const BatchArgs a) {
     __shared__ double s_v[kLaneWarps][32], s_w[kLaneWarps][32];
     __shared__ int s_item;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -264,16 +371,17 @@ __global__ void __launch_bounds__(kLaneThreads, d <= 5 ? 4 : 3) lane_kernel(cons
         const bool mv = mi < G.n_mem;
         const InstDesc& J = a.insts[__ldg(a.lane_members + G.mem_off + min(mi, G.n_mem - 1))];
         const LaneXBlock& XB = a.lane_xb[it.xblk];
-        const int ncols = XB.ncols;
-        const float* xl = a.lane_x + XB.off + lane;
-        const int cu = G.t_start - J.u - XB.t0;
+        // this lane's column base: the sample x_{t-u} of a point at window offset w is column
+        // t_start - u - t0 + w of repetition r (lane_xoff)
+        const float* xlq = a.lane_x + XB.off + lane + (size_t)(G.t_start - J.u - XB.t0) * 32;
+        const int ncols32 = XB.ncols * 32;
         const int64_t pt_off = J.pt_off;
         const unsigned nv = (unsigned)min(32, G.n_mem - it.mblock * 32);
         FF acc{0.0f, 0.0f};
         float acc_abs = 0.0f;
         const int qend = min(it.q0 + kLaneQB, G.N);
         for (int p = it.q0 + warp; p < qend; p += kLaneWarps)
-            lane_query<d, KS>(a, G, xl, ncols, cu, mv, nv, p, acc, acc_abs, pt_off);
+            lane_query<d, KS>(a, G, xlq, ncols32, mv, nv, p, acc, acc_abs, pt_off);
         s_v[warp][lane] = (double)acc.hi + (double)acc.lo;
         s_w[warp][lane] = (double)acc_abs;
         __syncthreads();

@@ -14,6 +14,7 @@ __global__ void lane_stage_kernel(const LaneGroup* __restrict__ groups, int n_gr
         const int NP = (G.N + 31) & ~31;
         const int DA = 1 + G.d, DA2 = (G.d + 2) / 2;
         for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < NP; p += gridDim.x * blockDim.x) {
+            float2* tp = tpart + G.tp_off + (size_t)(p >> 5) * (DA2 * 32) + (p & 31);  // chunk-major
             if (p < G.N) {
                 const int i = __ldg(sorted_idx + G.sort_off + p);
                 const int r = i / G.W, w = i - r * G.W;
@@ -23,11 +24,12 @@ __global__ void lane_stage_kernel(const LaneGroup* __restrict__ groups, int n_gr
                     const int c0 = 2 * c2, c1 = 2 * c2 + 1 < DA ? 2 * c2 + 1 : 1;
                     const float v0 = c0 == 0 ? __ldg(y + t) : __ldg(y + t - 1 - (c0 - 1) * G.tau);
                     const float v1 = __ldg(y + t - 1 - (c1 - 1) * G.tau);
-                    tpart[G.tp_off + (size_t)c2 * NP + p] = make_float2(v0, v1);
+                    tp[c2 * 32] = make_float2(v0, v1);
                 }
-                rw[G.sort_off + p] = (int32_t)(((uint32_t)r << 16) | (uint32_t)w);
+                rw[G.rw_off + p] = (int32_t)(((uint32_t)r << 16) | (uint32_t)w);
             } else {
-                for (int c2 = 0; c2 < DA2; ++c2) tpart[G.tp_off + (size_t)c2 * NP + p] = make_float2(f_inf(), f_inf());
+                for (int c2 = 0; c2 < DA2; ++c2) tp[c2 * 32] = make_float2(f_inf(), f_inf());
+                rw[G.rw_off + p] = 0;
             }
         }
     }
