@@ -3,19 +3,23 @@
 
 One step = one pass of the whole hot path (embedding gather, max-norm kNN search, marginal
 range counts, digamma sum, surrogate p-values) over one batch of synthetic input.  The default
-workload is the batched surrogate test: 400 trials of a coupled AR(2) pair, d = 3, tau = 1,
-u = 5, window 3 (N = 1200 points in a 7-D joint space), 50 analysis time points x (1 original
-+ 1000 trial-shuffled surrogates) = 50,050 estimates, k = 4.
+workload is the largest single-GPU configuration, the large-ensemble surrogate test: 4000
+trials of a logistic-map source driving an AR(1) target, d = 5, tau = 1, u = 5, window 3
+(N = 12,000 points in an 11-D joint space), 200 analysis time points x (1 original + 200
+trial-shuffled surrogates) = 40,200 estimates, k = 4.
 
 Printed (rank 0, one JSON line): combined max-norm pair evaluations per second (both passes,
 ordered pairs i != j) over all ranks, TE estimates per second, the end-to-end rate through the
-public API with host buffers, the per-instance-launch rate on the same GPU, the roofline of the
-persistent kernel against the FP32 ALU peak, the SM clocks seen, and the CPU oracle timed on a
-bounded sample of the same workload.
+public API with host buffers, per-instance launches against one batched launch on the same GPU,
+the roofline of the search kernels against the FP32 ALU peak (operations actually issued), the
+SM clocks seen, and the CPU oracle timed on a bounded sample of the same workload.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload c3]
-Under torchrun (N > 1) every rank runs the full workload on its own GPU (weak scaling, no
-collective on the data path); value = all ranks' pair evaluations / max-over-ranks time.
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload c5]
+                    [--scaling strong|weak]
+Under torchrun (N > 1) the ranks share the workload by default (strong scaling): each takes a
+cost-balanced share of the analysis time points (with all of their surrogates) and the results
+are all-gathered once per step, the only exchange; value = the workload's pair evaluations /
+max-over-ranks time. --scaling weak has every rank run the whole workload instead.
 """
 from __future__ import annotations
 
@@ -254,12 +258,60 @@ def cpu_baseline(w, seconds: float):
 
 
 # ---------------------------------------------------------------------------------- ours
+PATH_KERNELS = ("lane_kernel", "bundle_kernel", "batched_kernel")  # te_last_paths order
+
+
+def make_runner(te, torch, h, w, dev, units=None):
+    """The hot path on this rank: the whole workload, or (sharded) the units listed — analysis
+    starts of a surrogate test or delay scan, instances of a te_estimate batch. Returns (step,
+    outs, rows): step(series, outs) runs the library on this rank's share; rows(outs) packs its
+    results as float64 rows, one per unit (for the gather of a sharded run)."""
+    scan = scan_range(w)
+    surrogate = w.S > 0 and w.t_starts is not None
+    if scan or surrogate:
+        ts = list(w.t_starts[0]) if units is None else [w.t_starts[0][u] for u in units]
+        nt = len(ts)
+        if scan:
+            n_u = scan[1] - scan[0] + 1
+            outs = {"te": torch.empty((n_u, nt), dtype=torch.float64, device=dev),
+                    "p": torch.empty((n_u, nt), dtype=torch.float64, device=dev),
+                    "u_best": torch.empty(nt, dtype=torch.int32, device=dev)}
+
+            def step(series_dev, o):
+                return te.te_delay_scan(h, series_dev[0], ts, w.window, scan[0], scan[1], w.S, w.k, out=o)
+
+            def rows(o):
+                return torch.cat([o["te"].t(), o["p"].t(), o["u_best"].to(torch.float64).view(-1, 1)], dim=1)
+        else:
+            outs = {"te_orig": torch.empty((1, nt), dtype=torch.float64, device=dev),
+                    "te_surr": torch.empty((1, nt, w.S), dtype=torch.float64, device=dev),
+                    "p": torch.empty((1, nt), dtype=torch.float64, device=dev)}
+
+            def step(series_dev, o):
+                return te.te_surrogate_test(h, series_dev, ts, w.window, w.S, w.k, out=o)
+
+            def rows(o):
+                return torch.cat([o["te_orig"].view(-1, 1), o["p"].view(-1, 1), o["te_surr"].view(nt, w.S)], dim=1)
+        return step, outs, rows
+    insts = list(w.instances) if units is None else [w.instances[u] for u in units]
+    arr = te.instance_array(insts)  # host descriptors, built once like the device series
+    outs = torch.empty(len(insts), dtype=torch.float64, device=dev)
+
+    def step(series_dev, o):
+        return te.te_estimate(h, series_dev, arr, w.k, te=o)
+
+    def rows(o):
+        return o.view(-1, 1)
+    return step, outs, rows
+
+
 def bench_ours(args):
     import numpy as np
     import torch
     import torch.distributed as dist
     from paper_1401_4068_gb300 import build
     from paper_1401_4068_gb300 import inputs as I
+    from paper_1401_4068_gb300 import sharding
     from paper_1401_4068_gb300 import te
 
     ws, rank, local = dist_env()
@@ -281,38 +333,37 @@ def bench_ours(args):
     ds = te.to_device(w.series, dev)
     te.te_set_profiling(h, True)
     te.te_set_search(h, not args.exhaustive)
-    te.te_set_sharing(h, not args.no_sharing)
+    te.te_set_sharing(h, te.SHARE_NONE if args.no_sharing else te.SHARE_AUTO)
 
-    inst_arr = te.instance_array(w.instances)  # host descriptors, built once like the device series
+    # strong scaling (default with several ranks): each rank takes a cost-balanced share of the
+    # units and the per-unit results are all-gathered; weak: every rank runs the whole workload
+    sharded = ws > 1 and args.scaling == "strong"
+    units = parts = None
+    if sharded:
+        if scan or surrogate:
+            parts = sharding.balance(sharding.time_point_costs(w), ws)
+            n_units = len(w.t_starts[0])
+        else:
+            parts = sharding.shard(w, ws)
+            n_units = len(w.instances)
+        units = parts[rank]
+    step_local, outs, rows = make_runner(te, torch, h, w, dev, units)
+    if sharded and not units:
+        raise SystemExit(f"rank {rank} has no work: fewer units than ranks")
 
-    def step(series_dev, outs=None):
-        if scan:
-            return te.te_delay_scan(h, series_dev[0], w.t_starts[0], w.window, scan[0], scan[1], w.S, w.k,
-                                    out=outs)
-        if surrogate:
-            return te.te_surrogate_test(h, series_dev, w.t_starts[0], w.window, w.S, w.k, out=outs)
-        return te.te_estimate(h, series_dev, inst_arr, w.k, te=outs)
+    def step(series_dev, o):
+        step_local(series_dev, o)
+        if sharded:
+            return sharding.gather_rows(rows(o), parts, n_units)
+        return None
 
     tuned = None
     if args.shape:
         tuned = tuple(int(v) for v in args.shape.lower().split("x"))
         te.te_set_launch_config(h, tuned[0], tuned[1])
     elif not args.no_autotune:
-        tuned = te.te_autotune(h, ds, w.instances, w.k)
-    outs = None
-    if scan:
-        n_u = scan[1] - scan[0] + 1
-        nt = len(w.t_starts[0])
-        outs = {"te": torch.empty((n_u, nt), dtype=torch.float64, device=dev),
-                "p": torch.empty((n_u, nt), dtype=torch.float64, device=dev),
-                "u_best": torch.empty(nt, dtype=torch.int32, device=dev)}
-    elif surrogate:
-        nt = len(w.t_starts[0])
-        outs = {"te_orig": torch.empty((1, nt), dtype=torch.float64, device=dev),
-                "te_surr": torch.empty((1, nt, w.S), dtype=torch.float64, device=dev),
-                "p": torch.empty((1, nt), dtype=torch.float64, device=dev)}
-    else:
-        outs = torch.empty(len(w.instances), dtype=torch.float64, device=dev)
+        tuned = te.te_autotune(h, ds, w.instances if units is None or scan or surrogate else
+                               [w.instances[u] for u in units], w.k)
 
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
@@ -346,6 +397,7 @@ def bench_ours(args):
     clocks = sampler.stop()
     exec_pairs, exec_ops, swept = te.te_last_work(h)
     alu_ops, bundles = te.te_last_alu_ops(h)
+    paths = te.te_last_paths(h)
     (pass_pairs, pass_cycles) = te.te_last_pass_work(h)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
@@ -355,64 +407,78 @@ def bench_ours(args):
         total_ms = float(t.item())
     te.te_sync_status(h)
 
+    # units of work: the whole workload once per step (sharded), or once per rank (replicated)
+    copies = 1 if sharded else ws
     pe_step = 2 * pair_evals(w)
     n_est = len(w.instances) * _scan_factor(w)
-    value = ws * pe_step * args.steps / (total_ms / 1e3)
-    te_rate = ws * n_est * args.steps / (total_ms / 1e3)
+    value = copies * pe_step * args.steps / (total_ms / 1e3)
+    te_rate = copies * n_est * args.steps / (total_ms / 1e3)
+    # this rank's share of the pair evaluations (for its own device-side counters)
+    if sharded and (scan or surrogate):
+        pe_rank = pe_step * len(units) / len(w.t_starts[0])
+    elif sharded:
+        pe_rank = 2 * _scan_factor(w) * sum(w.n_points(w.instances[u]) * (w.n_points(w.instances[u]) - 1)
+                                            for u in units)
+    else:
+        pe_rank = pe_step
 
     # ---- the two passes: the step time split by the warps' SM cycles in each pass (device clock,
     # counted by the sweep); the algorithmic work is N (N - 1) pairs per pass
     passes = None
     if swept and sum(pass_cycles) > 0:
-        per_pass = pe_step / 2
+        per_pass = pe_rank / 2
         passes = {"time_split": "step time x share of the warps' SM cycles spent in the pass (clock64 on "
                                 "the device; pass 2 includes the digamma terms)"}
         for name, pp, cyc in (("pass1_knn", pass_pairs[0], pass_cycles[0]),
                               ("pass2_counts", pass_pairs[1], pass_cycles[1])):
             share = cyc / sum(pass_cycles)
             passes[name] = {"cycle_share": round(share, 4),
-                            "pair_evals_per_s": ws * per_pass * args.steps / (total_ms * share / 1e3),
+                            "pair_evals_per_s": copies * (pe_step / 2) * args.steps / (total_ms * share / 1e3),
                             "pair_evals_executed_per_step": pp,
                             "executed_vs_algorithmic": round(pp / max(1.0, per_pass), 4)}
 
-    # ---- roofline of the search kernel (CUDA events on its own stream, live): the bundle kernel
-    # when target-part sharing formed bundles, else the persistent batched kernel
+    # ---- roofline of the search kernels (CUDA events the library records around them on the
+    # launching stream, live): `frac` counts the FP32 subtract / abs-max operations the kernels
+    # actually issued; the kernel named is the one that ran most of the estimates
     kms = statistics.mean(kernel_ms)
-    ops = exec_ops  # 2 D FP32 operations per evaluated (query, reference, estimate) pair
-    achieved = ops / (kms / 1e3) / 1e12
-    kernel = "bundle_kernel" if bundles else "batched_kernel"
+    kernel = PATH_KERNELS[max(range(3), key=lambda i: (paths[i], -i))]
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz") or FALLBACK_SM_MHZ)
     n_sm = props.multi_processor_count
     peak = n_sm * ALU_LANES_PER_SM * sm_max * 1e6 / 1e12
+    achieved = alu_ops / (kms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
             "frac": round(achieved / peak, 4),
             "peak_source": f"{n_sm} SMs x {ALU_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
                            f"({'MEASURED_PEAKS.json sm_max_mhz' if peaks.get('sm_max_mhz') else 'fallback clock'})",
-            "op": "FP32 subtract or abs-max, 2*D per evaluated (query, reference) pair, both passes",
+            "op": "FP32 subtract / abs-max operations the search kernels issued (target parts computed "
+                  "once for the estimates that share them; references skipped by the exact shared "
+                  "bound not evaluated)",
             "kernel": kernel, "kernel_ms": round(kms, 4),
-            "traffic": traffic_per_launch(w, kernel),
-            # what the ALU actually executed: with target-part sharing the target part's 2 (1 + d)
-            # operations of a pair run once per bundle of estimates
+            "traffic": traffic_per_launch(w, kernel) if not sharded else None,
             "alu_ops_executed": alu_ops,
-            "alu_frac_executed": round(alu_ops / (kms / 1e3) / 1e12 / peak, 4)}
+            # 2 D operations per (query, reference, estimate) pair the kernels decided: the
+            # algorithmic unit, which counts shared and skipped operations as if executed
+            "frac_2d_per_decided_pair": round(exec_ops / (kms / 1e3) / 1e12 / peak, 4)}
     if clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = round(achieved / (n_sm * ALU_LANES_PER_SM * clocks["sm_mhz"] * 1e6 / 1e12), 4)
 
     # ---- end to end through the public API: pinned host inputs in, results out, every step
-    import torch as _t
     host = []
     for s in w.series:
-        hs = {"src": _t.from_numpy(np.ascontiguousarray(s.src)).pin_memory(),
-              "tgt": _t.from_numpy(np.ascontiguousarray(s.tgt)).pin_memory(),
-              "perms": None if s.perms is None else _t.from_numpy(np.ascontiguousarray(s.perms)).pin_memory()}
+        hs = {"src": torch.from_numpy(np.ascontiguousarray(s.src)).pin_memory(),
+              "tgt": torch.from_numpy(np.ascontiguousarray(s.tgt)).pin_memory(),
+              "perms": None if s.perms is None else torch.from_numpy(np.ascontiguousarray(s.perms)).pin_memory()}
         host.append(hs)
     h2d = sum(v.numel() * v.element_size() for hs in host for v in hs.values() if v is not None)
-    if isinstance(outs, dict):
-        out_host = {k: _t.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in outs.items()}
+    res_dev = step(ds, outs)
+    if res_dev is not None:
+        out_host = torch.empty(res_dev.shape, dtype=res_dev.dtype).pin_memory()
+    elif isinstance(outs, dict):
+        out_host = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in outs.items()}
     else:
-        out_host = _t.empty(outs.shape, dtype=outs.dtype).pin_memory()
-    d2h = (sum(v.numel() * v.element_size() for v in out_host.values()) if isinstance(outs, dict)
+        out_host = torch.empty(outs.shape, dtype=outs.dtype).pin_memory()
+    d2h = (sum(v.numel() * v.element_size() for v in out_host.values()) if isinstance(out_host, dict)
            else out_host.numel() * out_host.element_size())
 
     def e2e_step():
@@ -421,8 +487,10 @@ def bench_ours(args):
             s.tgt.copy_(hs["tgt"], non_blocking=True)
             if hs["perms"] is not None:
                 s.perms.copy_(hs["perms"], non_blocking=True)
-        step(ds, outs)
-        if isinstance(outs, dict):
+        r = step(ds, outs)
+        if r is not None:
+            out_host.copy_(r, non_blocking=True)
+        elif isinstance(outs, dict):
             for k in outs:
                 out_host[k].copy_(outs[k], non_blocking=True)
         else:
@@ -445,14 +513,17 @@ def bench_ours(args):
         t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
-    e2e = {"value": ws * pe_step * e2e_steps / (e2e_ms / 1e3), "unit": "pair-evals/s",
+    e2e = {"value": copies * pe_step * e2e_steps / (e2e_ms / 1e3), "unit": "pair-evals/s",
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-           "te_estimates_per_s": ws * n_est * e2e_steps / (e2e_ms / 1e3),
+           "te_estimates_per_s": copies * n_est * e2e_steps / (e2e_ms / 1e3),
            "ms_per_step": e2e_ms / e2e_steps}
 
-    # ---- per-instance launches of the same kernel, same GPU and stream, on a sub-batch
+    # ---- per-instance launches against one batched launch on a sub-batch, same GPU and stream:
+    # (a) one launch per estimate of the unshared persistent kernel, (b) one launch of the same
+    # kernel for the whole sub-batch (the like-for-like ratio: same kernel, same staging), (c) the
+    # default batched path (target parts shared)
     per = None
-    if not args.no_per_launch:
+    if not args.no_per_launch and ws == 1:
         if surrogate:
             per_t = lane_ops(w) // len(w.t_starts[0])
             n_t_sub = max(1, min(len(w.t_starts[0]), args.per_launch_instances // ((w.S + 1) * _scan_factor(w))))
@@ -464,41 +535,33 @@ def bench_ours(args):
                 wsub.extra = dict(u_lo=scan[0], u_hi=scan[0] + n_u_sub - 1)
         else:
             wsub = I.Workload(w.name, w.series, w.instances[: args.per_launch_instances], w.k)
-
-        sub_arr = te.instance_array(wsub.instances)
-
-        def sub_step(o=None):
-            if scan:
-                sr = scan_range(wsub)
-                return te.te_delay_scan(h, ds[0], wsub.t_starts[0], wsub.window, sr[0], sr[1], wsub.S, wsub.k)
-            if surrogate:
-                return te.te_surrogate_test(h, ds, wsub.t_starts[0], wsub.window, wsub.S, wsub.k)
-            return te.te_estimate(h, ds, sub_arr, wsub.k)
-
-        res = {}
-        for mode in (True, False):
-            te.te_set_batching(h, mode)
-            sub_step()
+        sub_step, sub_outs, _ = make_runner(te, torch, h, wsub, dev)
+        arms = (("per_instance_launch", True, te.SHARE_NONE), ("batched_same_kernel", False, te.SHARE_NONE),
+                ("batched_default", False, te.SHARE_NONE if args.no_sharing else te.SHARE_AUTO))
+        pe_sub = 2 * pair_evals(wsub)
+        n_sub = len(wsub.instances) * _scan_factor(wsub)
+        per = {"instances": n_sub}
+        for name, per_inst, share in arms:
+            te.te_set_batching(h, per_inst)
+            te.te_set_sharing(h, share)
+            sub_step(ds, sub_outs)
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             flush.zero_()
             a.record()
-            sub_step()
+            sub_step(ds, sub_outs)
             b.record()
             torch.cuda.synchronize()
-            res[mode] = a.elapsed_time(b)
-            n_launch = te.te_last_launch_count(h)
-            res[(mode, "launches")] = n_launch
+            ms = a.elapsed_time(b)
+            pth = te.te_last_paths(h)
+            per[name] = {"value": pe_sub / (ms / 1e3), "unit": "pair-evals/s", "te_estimates_per_s": n_sub / (ms / 1e3),
+                         "ms": round(ms, 3), "kernel_launches": te.te_last_launch_count(h),
+                         "kernel_path": {k: v for k, v in zip(PATH_KERNELS, pth) if v},
+                         "launch": "one per estimate" if per_inst else "one persistent launch (CUDA graph)"}
         te.te_set_batching(h, False)
-        pe_sub = 2 * pair_evals(wsub)
-        per = {"instances": len(wsub.instances) * _scan_factor(wsub),
-               "per_instance_launch": {"value": pe_sub / (res[True] / 1e3), "unit": "pair-evals/s",
-                                       "te_estimates_per_s": len(wsub.instances) / (res[True] / 1e3),
-                                       "ms": round(res[True], 3), "kernel_launches": res[(True, "launches")]},
-               "batched_same_subset": {"value": pe_sub / (res[False] / 1e3), "unit": "pair-evals/s",
-                                       "ms": round(res[False], 3), "kernel_launches": res[(False, "launches")]},
-               }
-        per["batched_vs_per_launch"] = round(res[True] / res[False], 2)
+        te.te_set_sharing(h, te.SHARE_NONE if args.no_sharing else te.SHARE_AUTO)
+        per["batched_vs_per_launch"] = round(per["per_instance_launch"]["ms"] / per["batched_same_kernel"]["ms"], 2)
+        per["default_vs_per_launch"] = round(per["per_instance_launch"]["ms"] / per["batched_default"]["ms"], 2)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -507,18 +570,21 @@ def bench_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "dtype": "f32", "data": "synthetic",
+        "scaling": "strong" if sharded else "weak", "dtype": "f32", "data": "synthetic",
         "vs_baseline": (round(value / PAPER_CHUNK_TITAN_PAIR_RATE, 2) if args.workload == "paper-chunk" else None),
         "config": {"workload": spec["desc"], "estimates_per_step": n_est,
                    "pair_evals_per_step": pe_step, "k": w.k,
                    "l2": "256 MiB buffer written between timed steps (inputs smaller than L2)",
-                   "per_rank": "every rank runs the full workload (weak scaling)",
+                   "per_rank": ("a cost-balanced share of the analysis starts / estimates per rank, results "
+                                "all-gathered (strong scaling)") if sharded else
+                               ("every rank runs the full workload (weak scaling)" if ws > 1 else "one GPU"),
                    "launch_shape": None if tuned is None else {"threads": tuned[0], "queries_per_thread": tuned[1],
                                                                "chosen_by": "--shape" if args.shape else "te_autotune"}},
         "te_estimates_per_s": te_rate,
         "search": {"mode": "sorted sweep" if swept else "exhaustive",
+                   "paths": {k: v for k, v in zip(PATH_KERNELS, paths)},
                    "pair_evals_executed_per_step": exec_pairs,
-                   "executed_vs_algorithmic": round(exec_pairs / max(1, pe_step), 4),
+                   "executed_vs_algorithmic": round(exec_pairs / max(1, pe_rank), 4),
                    "passes": passes,
                    "target_part_sharing": {"bundles": bundles, "alu_ops_executed_per_step": alu_ops,
                                            "alu_ops_vs_2D_per_pair": round(alu_ops / max(1, exec_ops), 4)}},
@@ -579,7 +645,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c3")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c5")
+    ap.add_argument("--scaling", choices=["strong", "weak"], default="strong",
+                    help="with several ranks: shard the workload (strong) or replicate it (weak)")
     ap.add_argument("--per-launch-instances", type=int, default=2002)
     ap.add_argument("--no-per-launch", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")

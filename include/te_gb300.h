@@ -259,14 +259,14 @@ te_status te_last_paths(te_handle* h, int32_t* paths);
 te_status te_last_pass_work(te_handle* h, uint64_t* pairs, uint64_t* cycles);
 
 /* Batching mode of te_estimate / te_surrogate_test. per_instance = 0 (default): one persistent
- * launch for the whole batch, captured in a CUDA graph. per_instance = 1: the same kernel and
- * tables, launched once per instance with a grid of that instance's work items and no graph,
- * the way an unbatched implementation runs one search space per launch (the comparison of the
- * Implementation section's "several chunks per launch" design). Per instance, no estimate is
- * staged whole in shared memory and target parts are not shared, so those estimates' Eq. 9
- * partial sums are grouped differently: counts and eps are bit-identical in both modes, TE is
- * bit-identical where the batched launch takes the tiled path without sharing as well and
- * otherwise agrees within the two err_bound values. */
+ * launch for the whole batch, captured in a CUDA graph. per_instance = 1: the unshared persistent
+ * kernel and tables, launched once per instance with a grid of that instance's work items and no
+ * graph, the way an unbatched implementation runs one search space per launch (the comparison of
+ * the Implementation section's "several chunks per launch" design). Per instance, target parts
+ * are not shared (no lane kernel, no bundles); an estimate that fits shared memory is staged whole
+ * as in one launch. Counts and eps are bit-identical in both modes; TE is bit-identical to a
+ * batched launch without sharing (te_set_sharing(h, 0)) and otherwise agrees within the two
+ * err_bound values. */
 te_status te_set_batching(te_handle* h, int32_t per_instance);
 
 /* te_surrogate_test_static - te_surrogate_test for one series, for callers that cannot allocate

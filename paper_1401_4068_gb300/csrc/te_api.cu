@@ -426,7 +426,7 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
     if (sweep) {
         // every instance resident in shared memory (up to kResidentMaxBytes) when it fits there,
         // which lets warps balance the work; otherwise tiles of whole CTA query blocks
-        if (!h->per_instance && (int64_t)dmaxN * (int64_t)sizeof(float) <= kResidentMaxBytes) {
+        if ((int64_t)dmaxN * (int64_t)sizeof(float) <= kResidentMaxBytes) {
             P->smem_floats = std::max(P->smem_floats, dmaxN);
         } else {
             int need = P->smem_floats;
@@ -683,7 +683,7 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
         I.strip_off = 0;
         if (bundled[i] || laned[i]) continue;
         const bool fits = (int64_t)((I.N + 3) & ~3) * (1 + 2 * I.d) <= P->smem_floats;
-        I.warp_mode = (sweep && fits && !h->per_instance) ? 1 : 0;
+        I.warp_mode = (sweep && fits) ? 1 : 0;
     }
     // sort groups: one per (target series, repetitions, window start, window); a group whose every
     // estimate takes a strip-aware path and agrees on the second key is cut into strips
