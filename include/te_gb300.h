@@ -227,11 +227,14 @@ te_status te_last_work(te_handle* h, uint64_t* pairs, uint64_t* ops, int32_t* sw
  * distance and count once for several estimates. The paper computes each surrogate separately;
  * this is exact because max is exact: each estimate sees the same FP32 differences the unshared
  * search computes.
- *   enable = 1 (default): groups of at least 8 such estimates with d = 2..8 run one estimate per
+ *   enable = 1 (default): groups of at least 32 such estimates with d = 4..8 run one estimate per
  *     lane (a warp takes one query point for 32 estimates; a reference whose target-part distance
  *     already reaches every lane's current radius is skipped for all 32 before any source
- *     coordinate is read); smaller groups with d <= 5 run in bundles of up to 3 staged together in
- *     shared memory (one embedding dimension per batch, the most frequent among them).
+ *     coordinate is read); other groups of two or more with d <= 5 run in bundles of up to 3
+ *     staged together in shared memory (one embedding dimension per batch, the most frequent
+ *     among them). The lane kernel measured faster than bundles for those groups only.
+ *   enable = 3: the lane kernel for every group of at least 8 estimates with d = 2..8, bundles
+ *     for the other groups.
  *   enable = 2: bundles only (no lane kernel).
  *   enable = 0: no sharing.
  * Sharing applies with k <= 4; every other estimate runs unshared. TE_EINVAL for other values. */
@@ -275,11 +278,14 @@ te_status te_set_batching(te_handle* h, int32_t per_instance);
  * pool, a fixed memory budget, code that must not cause the implicit synchronisation an
  * allocation can bring). It needs no handle and allocates nothing on the device or the host.
  * Its scratch (work-queue head, per-item partial sums, per-estimate TE, digamma table) is one
- * fixed static device array of about 2.6 MiB that every GPU loading the library holds until
- * the process exits.
+ * fixed static device array of about 2.6 MiB that every GPU using it holds until the process
+ * exits.
  *   Runs on the calling thread's current device. The first call on a device sets it up (looks
- *   up the array's device address, fills the digamma table, sets kernel attributes): make that
- *   call before any stream capture. Calls reuse the array; the queue head is cleared on each
+ *   up the array's device address, fills the digamma table and waits for that on `stream`, sets
+ *   kernel attributes). With the CUDA driver's lazy module loading, that first call is also when
+ *   the driver maps the array and its kernels on the device, which allocates device memory and
+ *   may synchronise: make the first call on each device where that is acceptable (at start-up),
+ *   and before any stream capture; later calls allocate nothing. Calls reuse the array; the queue head is cleared on each
  *   call and every other value is rewritten before it is read. Calls whose GPU work overlaps
  *   (other streams or host threads) race on the array and must be serialised by the caller.
  *   Limits: k <= 4, d = 1..5, N = R * window <= 8192, n_t <= 256, n_t * (S + 1) <= 65536

@@ -459,7 +459,8 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
     // members read their source part from member-minor arrays (LaneXBlock), shared by blocks with
     // the same source series and pairings; past kLaneXMaxBytes of such arrays no lanes are used.
     std::vector<char> laned(n_inst, 0);
-    if (sweep && h->sharing == 1 && !h->per_instance && ks == 5) {
+    if (sweep && (h->sharing == 1 || h->sharing == 3) && !h->per_instance && ks == 5) {
+        const bool all_lanes = h->sharing == 3;
         typedef std::tuple<const float*, int, int, int, int, int, int> TK;
         std::map<TK, std::vector<int>> by_target;
         std::vector<TK> korder;
@@ -482,7 +483,8 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
         std::vector<std::vector<int>> cand_xb;  // their blocks' X block
         for (const auto& key : korder) {
             const std::vector<int>& v = by_target[key];
-            if ((int)v.size() < te::kLaneMinMembers) continue;
+            if ((int)v.size() < (all_lanes ? te::kLaneMinMembers : te::kLaneAutoMembers)) continue;
+            if (!all_lanes && P->insts[v[0]].d < te::kLaneAutoMinD) continue;
             std::vector<int> blocks;
             for (size_t b = 0; b * 32 < v.size(); ++b) {
                 std::vector<uintptr_t> sig;
@@ -1645,7 +1647,7 @@ TE_EXPORT te_status te_last_work(te_handle* h, uint64_t* pairs, uint64_t* ops, i
 TE_EXPORT te_status te_set_sharing(te_handle* h, int32_t enable) {
     if (!h) return TE_EINVAL;
     h->err.clear();
-    if (enable < 0 || enable > 2) return h->fail(TE_EINVAL, "te_set_sharing: %d is not 0, 1 or 2", enable);
+    if (enable < 0 || enable > 3) return h->fail(TE_EINVAL, "te_set_sharing: %d is not 0, 1, 2 or 3", enable);
     h->sharing = enable;
     return TE_OK;
 }

@@ -5,8 +5,10 @@
 // implicit device synchronisation, or a process whose allocator is owned by someone else.
 // This entry point allocates nothing, on the device or the host. Its scratch space (work-queue
 // head, per-item partial sums, per-estimate TE values and the digamma table) is one
-// file-scope static device array of fixed size, loaded with the library and held by every GPU
-// that loads it until the process exits. The caller still provides inputs and outputs.
+// file-scope static device array of fixed size. The CUDA driver maps it, with this file's
+// kernels, when the module is first used on a device (with lazy module loading: the first call
+// of this entry point there), and every GPU keeps it until the process exits. The caller still
+// provides inputs and outputs.
 //
 // Limits (checked before any launch, TE_ENOTIMPL with a message when exceeded):
 //   one series, k <= 4, d = 1..5, N = R * window <= 8192 points, n_t <= 256 start points,
@@ -15,8 +17,10 @@
 //
 // The first call on a device sets that device up: with the device current it resolves the
 // array's device address with cudaGetSymbolAddress (the array's name in host code is only a
-// host-side stand-in), fills the digamma table with a small kernel and sets the kernels'
-// shared-memory attribute. Make that first call before any stream capture. Every later call
+// host-side stand-in), fills the digamma table with a small kernel, waits for it on the
+// caller's stream and sets the kernels' shared-memory attribute. That first call is where the
+// driver maps the array (a device allocation of its own, possibly with a synchronisation), so
+// make it where that is acceptable, and before any stream capture. Every later call
 // reuses the same array and keeps the previous call's contents; the queue head is cleared at
 // the start of each call, and every partial sum and TE value is rewritten before it is read.
 // Calls whose work overlaps on the GPU (other streams, other host threads) race on the array.
@@ -237,7 +241,10 @@ TE_EXPORT te_status te_surrogate_test_static(const te_series* s, const int32_t* 
                                               16384 * (int)sizeof(float))) != cudaSuccess)
                     return na_msg(msg, msg_len, TE_ECUDA, "cudaFuncSetAttribute failed");
             na_psi_kernel<<<(kNaMaxN + 2 + 255) / 256, 256, 0, st>>>(static_cast<unsigned char*>(ptr));
-            if ((e = cudaGetLastError()) != cudaSuccess) return na_msg(msg, msg_len, TE_ECUDA, cudaGetErrorString(e));
+            // the table is complete before the device counts as set up: a later call on another
+            // stream must not find it half written, and a failed fill must not be reused
+            if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess)
+                return na_msg(msg, msg_len, TE_ECUDA, cudaGetErrorString(e));
             g_na_ptr[dev] = static_cast<unsigned char*>(ptr);
         }
     }

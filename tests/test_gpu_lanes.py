@@ -1,4 +1,5 @@
-"""One estimate per lane (the lane kernel): a group of at least 8 estimates that share y_t and y-
+"""One estimate per lane (the lane kernel, forced here with te.SHARE_LANES; by default it takes
+groups of at least 32 estimates with d >= 4): a group of at least 8 estimates that share y_t and y-
 (the original and its trial-shuffled surrogates, every scanned delay u) runs with a warp per
 query point and one estimate per lane; a reference whose target-part distance already reaches
 every lane's radius is skipped for all of them. Per-point radii and counts must equal the
@@ -44,7 +45,7 @@ def _series(rng, R, T, d, tau, u, S, ties=False):
 def _check_against_unshared_and_oracle(h, series, insts, k, n_lane, oracle_idx=None):
     ds = te.to_device(series)
     off, p0, _, _ = _run(h, ds, insts, k, te.SHARE_NONE)
-    on, p1, ops1, alg1 = _run(h, ds, insts, k, te.SHARE_AUTO)
+    on, p1, ops1, alg1 = _run(h, ds, insts, k, te.SHARE_LANES)
     assert p0[0] == 0 and p1[0] == n_lane
     assert ops1 < alg1
     assert torch.equal(off["counts"], on["counts"]) and torch.equal(off["eps"], on["eps"])
@@ -122,7 +123,7 @@ def test_mixed_batch_lanes_bundles_and_unshared(te_handle):
              [I.Instance(1, 90, 2, p) for p in range(-1, 3)] +       # 4: bundles of 2 + 2
              [I.Instance(0, 100, 4, -1), I.Instance(1, 110, 1, 0)])  # unshared
     ds = te.to_device([s2, s3])
-    on, paths, _, _ = _run(te_handle, ds, insts, 4, te.SHARE_AUTO)
+    on, paths, _, _ = _run(te_handle, ds, insts, 4, te.SHARE_LANES)
     assert paths == (23, 4, 2)
     off, _, _, _ = _run(te_handle, ds, insts, 4, te.SHARE_NONE)
     assert torch.equal(off["counts"], on["counts"]) and torch.equal(off["eps"], on["eps"])
@@ -145,9 +146,13 @@ def test_delay_scan_in_lanes_equals_unshared(te_handle):
         torch.cuda.synchronize()
     finally:
         te.te_set_sharing(te_handle, te.SHARE_AUTO)
-    on = te.te_delay_scan(te_handle, ds[0], starts, 4, 4, 8, 3, 4)
-    torch.cuda.synchronize()
-    assert te.te_last_paths(te_handle)[0] == 2 * 5 * 4
+    te.te_set_sharing(te_handle, te.SHARE_LANES)
+    try:
+        on = te.te_delay_scan(te_handle, ds[0], starts, 4, 4, 8, 3, 4)
+        torch.cuda.synchronize()
+        assert te.te_last_paths(te_handle)[0] == 2 * 5 * 4
+    finally:
+        te.te_set_sharing(te_handle, te.SHARE_AUTO)
     assert torch.max(torch.abs(off["te"] - on["te"])).item() <= 1e-9
     assert torch.equal(off["p"], on["p"]) and torch.equal(off["u_best"], on["u_best"])
     for iu, u in enumerate(range(4, 9)):
@@ -161,6 +166,7 @@ def test_bad_permutation_entry_in_lanes_is_flagged(te_handle):
     s = _series(rng, 30, 40, 2, 1, 2, 9)
     s.perms[4, 11] = s.R + 3
     ds = te.to_device([s])
+    te.te_set_sharing(te_handle, te.SHARE_LANES)
     te.te_estimate(te_handle, ds, [I.Instance(0, 10, 3, p) for p in range(-1, 3)] +
                    [I.Instance(0, 10, 3, p) for p in range(5, 9)], 4)
     assert te.te_last_paths(te_handle)[0] == 8
@@ -169,9 +175,30 @@ def test_bad_permutation_entry_in_lanes_is_flagged(te_handle):
     assert te.te_last_paths(te_handle)[0] == 10
     with pytest.raises(te.TEError, match="TE_EINVAL"):
         te.te_sync_status(te_handle)
+    te.te_set_sharing(te_handle, te.SHARE_AUTO)
+
+
+def test_default_rule_takes_large_groups_of_wide_estimates(te_handle):
+    """By default the lane kernel takes groups of 32 or more estimates with d >= 4 only."""
+    rng = np.random.default_rng(950)
+    s4 = _series(rng, 40, 60, 4, 1, 2, 40)
+    s3 = I.Series(s4.src, s4.tgt, d=3, tau=1, u=2, perms=s4.perms)
+    # 41 estimates with d = 4: lanes; the rest share in bundles of one d per batch, the d with
+    # the most of them (41 with d = 3 against 31 with d = 4), so the 31 run unshared
+    insts = ([I.Instance(0, 20, 2, p) for p in range(-1, 40)] +
+             [I.Instance(0, 30, 2, p) for p in range(-1, 30)] +
+             [I.Instance(1, 20, 2, p) for p in range(-1, 40)])
+    ds = te.to_device([s4, s3])
+    on, paths, _, _ = _run(te_handle, ds, insts, 4, te.SHARE_AUTO)
+    assert paths == (41, 41, 31)
+    o_te, o_counts, o_eps = oracle.te_batch([s4, s3], insts, 4, want_counts=True)
+    np.testing.assert_array_equal(on["counts"].cpu().numpy(), o_counts)
+    np.testing.assert_array_equal(on["eps"].cpu().numpy(), o_eps)
+    assert np.max(np.abs(on["te"].cpu().numpy() - o_te)) <= TOL
 
 
 def test_lanes_are_deterministic_and_replay(te_handle):
+    te.te_set_sharing(te_handle, te.SHARE_LANES)
     w = I.config(3, n_t=2, S=40)
     ds = te.to_device(w.series)
     a = te.te_surrogate_test(te_handle, ds, w.t_starts[0], w.window, w.S, w.k)
@@ -179,5 +206,6 @@ def test_lanes_are_deterministic_and_replay(te_handle):
     b = te.te_surrogate_test(te_handle, ds, w.t_starts[0], w.window, w.S, w.k)
     torch.cuda.synchronize()
     assert te.te_last_paths(te_handle)[0] == len(w.instances)
+    te.te_set_sharing(te_handle, te.SHARE_AUTO)
     for key in a:
         assert torch.equal(a[key], b[key])

@@ -3,15 +3,18 @@
 It keeps its scratch in a static device array instead of calling cudaMalloc.
 
 Called here through the C ABI (ctypes on the shared library) and checked against the
-allocating entry point te_surrogate_test on the same inputs, for two different calls in a
-row, so that a call that reuses the array left by the previous one is covered too. This file
-sorts last so that a run stopping at its first failure has run every other test first."""
+allocating entry point te_surrogate_test and against the CPU oracle on the same inputs, for two
+different calls in a row, so that a call that reuses the array left by the previous one is
+covered too; and a call after the first allocates no device memory (torch's allocator counters
+and the driver's free-memory figure are unchanged around it). This file sorts last so that a
+run stopping at its first failure has run every other test first."""
 import ctypes as C
 
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_1401_4068_gb300 import inputs as I
 from paper_1401_4068_gb300 import te
 
@@ -28,13 +31,17 @@ def _static_fn():
     return fn
 
 
-def _call_static(ds, t_starts, window, S, k):
+def _outputs(nt, S, dev):
+    return {"te_orig": torch.full((nt,), -1.0, dtype=torch.float64, device=dev),
+            "te_surr": torch.full((nt, max(S, 1)), -1.0, dtype=torch.float64, device=dev),
+            "p": torch.full((nt,), -1.0, dtype=torch.float64, device=dev)}
+
+
+def _call_static(ds, t_starts, window, S, k, out=None):
     fn = _static_fn()
-    dev = ds.src.device
     nt = len(t_starts)
-    out = {"te_orig": torch.full((nt,), -1.0, dtype=torch.float64, device=dev),
-           "te_surr": torch.full((nt, max(S, 1)), -1.0, dtype=torch.float64, device=dev),
-           "p": torch.full((nt,), -1.0, dtype=torch.float64, device=dev)}
+    if out is None:
+        out = _outputs(nt, S, ds.src.device)
     ts = (C.c_int32 * nt)(*t_starts)
     msg = C.create_string_buffer(256)
     desc = ds.desc()
@@ -76,8 +83,36 @@ def test_static_scratch_matches_allocating_entry_point():
             assert torch.max(torch.abs(got["te_orig"] - ref["te_orig"][0])).item() <= TOL
             assert torch.max(torch.abs(got["te_surr"][:, :S] - ref["te_surr"][0])).item() <= TOL
             assert torch.equal(got["p"], ref["p"][0])
+            # and directly against the oracle: TE within the tolerance, p-values equal
+            insts = [I.Instance(0, t, window, m) for t in t_starts for m in range(-1, S)]
+            o = oracle.te_batch([s], insts, case["k"]).reshape(len(t_starts), S + 1)
+            assert np.max(np.abs(got["te_orig"].cpu().numpy() - o[:, 0])) <= TOL
+            assert np.max(np.abs(got["te_surr"][:, :S].cpu().numpy() - o[:, 1:])) <= TOL
+            for j in range(len(t_starts)):
+                assert got["p"][j].item() == oracle.pvalue(o[j, 0], o[j, 1:])
     finally:
         h.close()
+
+
+def test_a_call_after_the_first_allocates_nothing():
+    """The property the entry point exists for: once a device is set up (first call), a call
+    changes neither torch's allocator counters nor the device's free memory."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    s, t_starts, window, S = _workload(CASES[0])
+    ds = te.to_device([s])[0]
+    st, msg, first = _call_static(ds, t_starts, window, S, 4)  # first call on the device: set-up
+    torch.cuda.synchronize()
+    assert st == te.TE_OK, msg
+    out = _outputs(len(t_starts), S, ds.src.device)  # outputs allocated before the measurement
+    torch.cuda.synchronize()
+    before = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved(), torch.cuda.mem_get_info()[0])
+    st, msg, second = _call_static(ds, t_starts, window, S, 4, out)
+    torch.cuda.synchronize()
+    after = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved(), torch.cuda.mem_get_info()[0])
+    assert st == te.TE_OK, msg
+    assert after == before
+    assert torch.equal(first["te_orig"], second["te_orig"]) and torch.equal(first["p"], second["p"])
 
 
 def test_static_rejects_sizes_beyond_its_scratch():
