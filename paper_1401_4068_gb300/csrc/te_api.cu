@@ -133,6 +133,7 @@ struct Plan {
     std::vector<int32_t> lmembers;
     int64_t tp_total = 0;          // float2 entries of the sorted target parts
     int64_t rw_total = 0;          // entries of the (repetition, sample) tables
+    int64_t ck_total = 0;          // entries of the chunk first-key tables
     std::vector<te::LaneXBlock> xblocks;
     int64_t x_total = 0, x_max = 0;  // floats of all / the largest member-minor source array
     int lane_max_np = 0;
@@ -207,7 +208,7 @@ struct te_handle {
     DevBuf<int32_t> d_lmembers, d_lrw;
     DevBuf<float2> d_tpart;
     DevBuf<te::LaneXBlock> d_lxb;
-    DevBuf<float> d_lx;
+    DevBuf<float> d_lx, d_lck;
     HostBuf<unsigned char> h_stage;
     int workspace_gen = 0;
 
@@ -552,6 +553,8 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
             P->tp_total += (int64_t)((I0.d + 2) / 2) * NP;
             G.rw_off = P->rw_total;
             P->rw_total += NP;
+            G.ck_off = P->ck_total;
+            P->ck_total += NP / 32;
             P->lane_max_np = std::max(P->lane_max_np, NP);
             const int nqb = (I0.N + te::kLaneQB - 1) / te::kLaneQB;
             for (int i : v) {
@@ -719,8 +722,9 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
                 const bool tiled_bundle = bundled[i] && I.warp_mode == 0;
                 const bool tiled_alone = !bundled[i] && I.warp_mode == 0 && te::kStripPoints % per == 0 &&
                                          (int64_t)te::kStripPoints * (1 + 2 * I.d) * 4 <= kSweepSmemMaxBytes;
-                if (lag != k2lag || !(resident_alone || resident_bundle || tiled_bundle || tiled_alone)) ok = false;
-                if (laned[i]) ok = false;  // the lane kernel sweeps one key order
+                // the lane kernel sweeps strips too (its estimates have d >= 2: the second key is in y-)
+                if (lag != k2lag || !(laned[i] || resident_alone || resident_bundle || tiled_bundle || tiled_alone))
+                    ok = false;
             }
             // strips of kStripPoints, for groups of 4 strips or more (shorter strips were measured
             // slower: a C3 group of 1200 points in 4 strips took 66.7 ms instead of 46.9 ms; the
@@ -738,14 +742,20 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
                 I.npad = npad;
                 I.strip_off = G.strip_off;
                 // a tiled estimate over strips stages a whole strip per tile
-                if (S > 1 && !bundled[i] && I.warp_mode == 0)
+                if (S > 1 && !bundled[i] && !laned[i] && I.warp_mode == 0)
                     P->smem_floats = std::max(P->smem_floats, te::kStripPoints * (1 + 2 * I.d));
             }
             P->sorted_total += npad;
             if (S > 1) strip_total += S + 1;
         }
         P->strip_total = strip_total;
-        for (auto& G : P->lgroups) G.sort_off = P->insts[P->lmembers[G.mem_off]].sort_off;
+        for (auto& G : P->lgroups) {
+            const InstDesc& I = P->insts[P->lmembers[G.mem_off]];
+            G.sort_off = I.sort_off;
+            G.strips = I.strips;
+            G.npad = I.npad;
+            G.strip_off = I.strip_off;
+        }
     }
     // tiled bundles: one work item per block of kBundleThreads * kBundleQ sorted positions
     {
@@ -944,7 +954,8 @@ te_status prepare_sweep(te_handle* h, const Plan& P, bool* grew) {
             (e = h->d_tpart.ensure((size_t)P.tp_total, grew)) != cudaSuccess ||
             (e = h->d_lrw.ensure((size_t)P.rw_total, grew)) != cudaSuccess ||
             (e = h->d_lxb.ensure(P.xblocks.size(), grew)) != cudaSuccess ||
-            (e = h->d_lx.ensure((size_t)P.x_total, grew)) != cudaSuccess)
+            (e = h->d_lx.ensure((size_t)P.x_total, grew)) != cudaSuccess ||
+            (e = h->d_lck.ensure((size_t)P.ck_total, grew)) != cudaSuccess)
             return h->fail(TE_ENOMEM, "lane workspace: %s", cudaGetErrorString(e));
     }
     return TE_OK;
@@ -989,6 +1000,7 @@ BatchArgs batch_args(te_handle* h, const Plan& P, int k, int32_t* counts, float*
             a.lane_members = h->d_lmembers.p;
             a.lane_xb = h->d_lxb.p;
             a.lane_x = h->d_lx.p;
+            a.lane_ckey = h->d_lck.p;
         }
     }
     return a;
@@ -1114,8 +1126,8 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
                                  h->cap_stream);
             if (ce == cudaSuccess)
                 ce = te::launch_lane_stage(h->d_lgroups.p, (int)P.lgroups.size(), P.lane_max_np, h->d_sidx.p,
-                                           h->d_tpart.p, h->d_lrw.p, h->d_lxb.p, (int)P.xblocks.size(), P.x_max,
-                                           h->d_lx.p, h->d_words.p + 1, h->cap_stream);
+                                           h->d_tpart.p, h->d_lrw.p, h->d_lck.p, h->d_lxb.p, (int)P.xblocks.size(),
+                                           P.x_max, h->d_lx.p, h->d_words.p + 1, h->cap_stream);
             ++launches;
         }
         // an event recorded during capture becomes a graph node only with cudaEventRecordExternal
@@ -1257,6 +1269,7 @@ TE_EXPORT void te_destroy(te_handle* h) {
     h->d_tpart.release();
     h->d_lxb.release();
     h->d_lx.release();
+    h->d_lck.release();
     h->h_stage.release();
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);

@@ -84,8 +84,11 @@ struct LaneGroup {
     int64_t sort_off;      // the group's sorted order (sorted_idx)
     int64_t tp_off;        // its sorted target part
     int64_t rw_off;        // its (repetition, sample) table
+    int64_t ck_off;        // the key of each chunk's first position (lane_ckey)
+    int64_t strip_off;     // strips > 1: its strip table (strip_pos / strip_k2, see SortGroup)
     int32_t R, T, W, t_start, N, d, tau;
     int32_t mem_off, n_mem;
+    int32_t strips, npad;  // the sort group's strips and sorted positions (with strip padding)
     int32_t reserved;
 };
 
@@ -151,6 +154,7 @@ struct BatchArgs {
     const int32_t* lane_members;
     const LaneXBlock* lane_xb;
     const float* lane_x;
+    const float* lane_ckey;
 };
 
 // ---- launchers (te_unit.cu) ----
@@ -203,8 +207,8 @@ const void* lane_ptr_lo(int d, int ks);
 const void* lane_ptr_hi(int d, int ks);
 cudaError_t launch_lanes(int d, int ks, const BatchArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_lane_stage(const LaneGroup* groups, int n_groups, int max_np, const int32_t* sorted_idx,
-                              float2* tpart, int32_t* lane_rw, const LaneXBlock* xblocks, int n_xblocks,
-                              int64_t max_x, float* lane_x, int32_t* flags, cudaStream_t s);
+                              float2* tpart, int32_t* lane_rw, float* lane_ckey, const LaneXBlock* xblocks,
+                              int n_xblocks, int64_t max_x, float* lane_x, int32_t* flags, cudaStream_t s);
 cudaError_t launch_finalize_te(const InstDesc* insts, int n_inst, const double* partial,
                                const double* partial_abs, double psi_k, double err_coef,
                                double* te, double* err, cudaStream_t s);

@@ -21,7 +21,9 @@
 // References are visited in the group's sorted order (key y_{t'-1}, see te_sweep.cuh): the
 // query's own 32-position chunk first, then chunks to the right and to the left while their keys
 // lie inside the window (key_q - thr, key_q + thr) with bounds rounded outward; pass 2 visits the
-// chunks of the window of the largest eps, a subset of those pass 1 visited.
+// chunks of the window of the largest eps. A group of 4096 points or more is cut into strips by
+// a second target coordinate (SortGroup): the sweeps then also skip whole strips whose second-key
+// range misses the window.
 #pragma once
 
 #include "te_sweep.cuh"
@@ -76,7 +78,7 @@ __device__ __forceinline__ float lane_join(float a, const u64 (&q2)[(d + 1) / 2]
 // d completed with coordinate 1 again; positions past N hold +inf. So a chunk's loads are one
 // pointer plus constant offsets, and the key y_{t'-1} of its first and last position are .y of its
 // row-0 entries 0 and 31. rw[32 ch + l] = r << 16 | w of the point at sorted position 32 ch + l
-// (0 past N).
+// (0 past N), ckey[ch] the key of the chunk's first position (+inf past N).
 template <int d>
 __device__ __forceinline__ void lane_load(const float2* __restrict__ cp, const int32_t* __restrict__ rwp,
                                           float2 (&r)[(d + 2) / 2], int32_t& rw) {
@@ -215,12 +217,16 @@ __device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& 
     constexpr int CH = DA2 * 32;      // float2 per chunk
     const int lane = threadIdx.x & 31;
     const int N = G.N, nch = (G.N + 31) >> 5;
+    const int S = G.strips;
     const float2* tpb = a.tpart + G.tp_off;  // uniform base; tpb + lane: this lane's column
     const float2* tpl = tpb + lane;
     const int32_t* rwl = a.lane_rw + G.rw_off + lane;
+    const float* ckl = a.lane_ckey + G.ck_off + lane;
+    const int32_t* spos = a.strip_pos + G.strip_off;
+    const float* sk2 = a.strip_k2 + 2 * G.strip_off;
     const int tau32 = G.tau * 32;
 
-    // the query (uniform): target coordinates and key; the lane's source part
+    // the query (uniform): target coordinates, key and second key; the lane's source part
     const int pc = p >> 5;
     u64 tq[DA2];
 #pragma unroll
@@ -228,10 +234,21 @@ __device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& 
         const float2 q = __ldg(tpb + pc * CH + c2 * 32 + (p & 31));
         tq[c2] = pack2(q.x, q.y);
     }
-    float keyq, tmp;
+    float keyq, k2q, tmp;
     split2(tq[0], tmp, keyq);
+    split2(tq[1], k2q, tmp);  // coordinate 2, y_{t'-1-tau}: the strips' second key (d >= 2)
     u64 xq[P];
     lane_source<d>(xlq + lane_xoff((uint32_t)__ldg(a.lane_rw + G.rw_off + p), ncols32), tau32, xq);
+
+    // With strips (S > 1; strip s = chunks 32 s .. 32 s + 31, sorted by y_{t'-1} inside, strips in
+    // order of the second key): where a key window starts in strip s. Lane l holds the first key
+    // of the strip's chunk l; the window starts at the last chunk whose first key is <= lb.
+    auto strip_start = [&](int s, float lb, float& fk, int& ce) {
+        const int cs = s << 5;
+        ce = min(nch, (__ldg(spos + s + 1) + 31) >> 5);
+        fk = cs + lane < ce ? __ldg(ckl + cs) : f_inf();
+        return cs + max(0, __popc(__ballot_sync(0xffffffffu, fk <= lb)) - 1);
+    };
 
     pass1_begin(a);
     unsigned vis1 = 0, pas1 = 0;
@@ -239,9 +256,8 @@ __device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& 
 #pragma unroll
     for (int s = 0; s < KS; ++s) t[s] = f_inf();
     float thr = f_inf();
-    int chl = pc, chr = pc;
     // one chunk (a reference per lane; its data r, rw already loaded): the target-part distance dT,
-    // then every reference with dT < thr for all lanes, two per round (independent loads)
+    // then every reference with dT < thr for all lanes
     auto scan1 = [&](const float2 (&r)[DA2], int32_t rwv, int ch) {
         float v[2 * DA2];
         lane_diff<d>(r, tq, v);
@@ -260,54 +276,123 @@ __device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& 
     // position from its loaded row 0. A prefetched chunk past the window is not used.
     float2 cur[DA2], nxt[DA2];
     int32_t rwc, rwn;
+    // own strip (the whole group without strips): outward from the query's chunk
+    int cs0 = 0, ce0 = nch;
+    if (S > 1) {
+        cs0 = pc & ~31;
+        ce0 = min(nch, (__ldg(spos + (pc >> 5) + 1) + 31) >> 5);
+    }
+    int chl = pc, chr = pc;
     lane_load<d>(tpl + pc * CH, rwl + (pc << 5), cur, rwc);
-    if (pc + 1 < nch) lane_load<d>(tpl + (pc + 1) * CH, rwl + ((pc + 1) << 5), nxt, rwn);
+    if (pc + 1 < ce0) lane_load<d>(tpl + (pc + 1) * CH, rwl + ((pc + 1) << 5), nxt, rwn);
     scan1(cur, rwc, pc);
-    for (int ch = pc + 1; ch < nch; ++ch) {  // right: stop at the first chunk starting outside
+    for (int ch = pc + 1; ch < ce0; ++ch) {  // right: stop at the first chunk starting outside
 #pragma unroll
         for (int c2 = 0; c2 < DA2; ++c2) cur[c2] = nxt[c2];
         rwc = rwn;
         if (!(__shfl_sync(0xffffffffu, cur[0].y, 0) < __fadd_ru(keyq, thr))) break;
-        if (ch + 1 < nch) lane_load<d>(tpl + (ch + 1) * CH, rwl + ((ch + 1) << 5), nxt, rwn);
+        if (ch + 1 < ce0) lane_load<d>(tpl + (ch + 1) * CH, rwl + ((ch + 1) << 5), nxt, rwn);
         scan1(cur, rwc, ch);
         chr = ch;
     }
-    if (pc > 0) lane_load<d>(tpl + (pc - 1) * CH, rwl + ((pc - 1) << 5), nxt, rwn);
-    for (int ch = pc - 1; ch >= 0; --ch) {  // left: stop at the first chunk ending outside
+    if (pc > cs0) lane_load<d>(tpl + (pc - 1) * CH, rwl + ((pc - 1) << 5), nxt, rwn);
+    for (int ch = pc - 1; ch >= cs0; --ch) {  // left: stop at the first chunk ending outside
 #pragma unroll
         for (int c2 = 0; c2 < DA2; ++c2) cur[c2] = nxt[c2];
         rwc = rwn;
         if (!(__shfl_sync(0xffffffffu, cur[0].y, 31) > __fsub_rd(keyq, thr))) break;
-        if (ch > 0) lane_load<d>(tpl + (ch - 1) * CH, rwl + ((ch - 1) << 5), nxt, rwn);
+        if (ch > cs0) lane_load<d>(tpl + (ch - 1) * CH, rwl + ((ch - 1) << 5), nxt, rwn);
         scan1(cur, rwc, ch);
         chl = ch;
+    }
+    // the other strips nearest first in the second key, while their second-key range meets the
+    // window; in each, the chunks of the key window (both keys are coordinates of y-, so a
+    // reference outside either window has dT >= thr and could not enter any list)
+    if (S > 1) {
+        const int s0 = pc >> 5;
+        bool up = s0 + 1 < S, down = s0 > 0;
+        for (int step = 1; up || down; ++step) {
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const int s = side == 0 ? s0 + step : s0 - step;
+                if (side == 0 ? (!up || s >= S) : (!down || s < 0)) {
+                    if (side == 0) up = false;
+                    else down = false;
+                    continue;
+                }
+                if (side == 0 && !(__ldg(sk2 + 2 * s) < __fadd_ru(k2q, thr))) {
+                    up = false;
+                    continue;
+                }
+                if (side == 1 && !(__ldg(sk2 + 2 * s + 1) > __fsub_rd(k2q, thr))) {
+                    down = false;
+                    continue;
+                }
+                float fk;
+                int ce;
+                const int c0 = strip_start(s, __fsub_rd(keyq, thr), fk, ce);
+                lane_load<d>(tpl + c0 * CH, rwl + (c0 << 5), nxt, rwn);
+                for (int ch = c0; ch < ce; ++ch) {
+#pragma unroll
+                    for (int c2 = 0; c2 < DA2; ++c2) cur[c2] = nxt[c2];
+                    rwc = rwn;
+                    if (!(__shfl_sync(0xffffffffu, fk, ch - (s << 5)) < __fadd_ru(keyq, thr))) break;
+                    if (ch + 1 < ce) lane_load<d>(tpl + (ch + 1) * CH, rwl + ((ch + 1) << 5), nxt, rwn);
+                    scan1(cur, rwc, ch);
+                }
+            }
+        }
     }
     const float e = topk_select(t, a.k);
     const float emax = lanes_max(mv ? e : 0.0f);
     pass1_end(a, (unsigned long long)vis1 * nv);
 
-    // ---- pass 2: chunks of the window of the largest eps (inside those pass 1 visited)
+    // ---- pass 2: the chunks of the window of the largest eps (without strips inside those pass 1
+    // visited; with strips, in every strip whose second-key range meets the window)
     const float lb = __fsub_rd(keyq, emax), rb = __fadd_ru(keyq, emax);
     float cz = 0.0f, cyz = 0.0f, cxz = 0.0f;
     unsigned vis2 = 0, pas2 = 0;
-    lane_load<d>(tpl + chl * CH, rwl + (chl << 5), nxt, rwn);
-    for (int ch = chl; ch <= chr; ++ch) {
-#pragma unroll
-        for (int c2 = 0; c2 < DA2; ++c2) cur[c2] = nxt[c2];
-        rwc = rwn;
-        if (!(__shfl_sync(0xffffffffu, cur[0].y, 0) < rb)) break;
-        if (ch < chr) lane_load<d>(tpl + (ch + 1) * CH, rwl + ((ch + 1) << 5), nxt, rwn);
-        if (!(__shfl_sync(0xffffffffu, cur[0].y, 31) > lb)) continue;  // padding (+inf) never skips
+    auto scan2 = [&](const float2 (&r)[DA2], int32_t rwv, int ch) {
         float v[2 * DA2];
-        lane_diff<d>(cur, tq, v);
+        lane_diff<d>(r, tq, v);
         const float bv = absmax_range<1, 2 * DA2 - 1>(v);  // y- (and the repeated coordinate 1)
         const float ayz = fabsf(v[0]);                     // y_t (joined with b per reference)
         unsigned ball = __ballot_sync(0xffffffffu, bv < emax);
         vis2 += min(32, N - (ch << 5));
         if (ball) {
-            const int xo = lane_xoff((uint32_t)rwc, ncols32);
+            const int xo = lane_xoff((uint32_t)rwv, ncols32);
             pas2 += __popc(ball);
             lane_count_refs<d, lane_round<d>()>(ball, bv, ayz, xo, xlq, tau32, xq, e, cz, cyz, cxz);
+        }
+    };
+    if (S > 1) {
+        const float lb2 = __fsub_rd(k2q, emax), rb2 = __fadd_ru(k2q, emax);
+        for (int s = 0; s < S; ++s) {
+            if (!(__ldg(sk2 + 2 * s + 1) > lb2)) continue;  // strip entirely below the window
+            if (!(__ldg(sk2 + 2 * s) < rb2)) break;         // this and every later strip above it
+            float fk;
+            int ce;
+            const int c0 = strip_start(s, lb, fk, ce);
+            lane_load<d>(tpl + c0 * CH, rwl + (c0 << 5), nxt, rwn);
+            for (int ch = c0; ch < ce; ++ch) {
+#pragma unroll
+                for (int c2 = 0; c2 < DA2; ++c2) cur[c2] = nxt[c2];
+                rwc = rwn;
+                if (!(__shfl_sync(0xffffffffu, fk, ch - (s << 5)) < rb)) break;
+                if (ch + 1 < ce) lane_load<d>(tpl + (ch + 1) * CH, rwl + ((ch + 1) << 5), nxt, rwn);
+                scan2(cur, rwc, ch);
+            }
+        }
+    } else {
+        lane_load<d>(tpl + chl * CH, rwl + (chl << 5), nxt, rwn);
+        for (int ch = chl; ch <= chr; ++ch) {
+#pragma unroll
+            for (int c2 = 0; c2 < DA2; ++c2) cur[c2] = nxt[c2];
+            rwc = rwn;
+            if (!(__shfl_sync(0xffffffffu, cur[0].y, 0) < rb)) break;
+            if (ch < chr) lane_load<d>(tpl + (ch + 1) * CH, rwl + ((ch + 1) << 5), nxt, rwn);
+            if (!(__shfl_sync(0xffffffffu, cur[0].y, 31) > lb)) continue;  // padding (+inf) never skips
+            scan2(cur, rwc, ch);
         }
     }
     pass2_end(a);

@@ -8,15 +8,16 @@ namespace te {
 // Pre-pass: the sorted target part and (r, w) of every point of every lane group.
 __global__ void lane_stage_kernel(const LaneGroup* __restrict__ groups, int n_groups,
                                   const int32_t* __restrict__ sorted_idx, float2* __restrict__ tpart,
-                                  int32_t* __restrict__ rw) {
+                                  int32_t* __restrict__ rw, float* __restrict__ ckey) {
     for (int g = blockIdx.y; g < n_groups; g += gridDim.y) {
         const LaneGroup G = groups[g];
         const int NP = (G.N + 31) & ~31;
         const int DA = 1 + G.d, DA2 = (G.d + 2) / 2;
         for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < NP; p += gridDim.x * blockDim.x) {
             float2* tp = tpart + G.tp_off + (size_t)(p >> 5) * (DA2 * 32) + (p & 31);  // chunk-major
-            if (p < G.N) {
-                const int i = __ldg(sorted_idx + G.sort_off + p);
+            // positions past N (and the strip padding, index -1, which lies there) are padding
+            const int i = p < G.N ? __ldg(sorted_idx + G.sort_off + p) : -1;
+            if (i >= 0) {
                 const int r = i / G.W, w = i - r * G.W;
                 const int t = G.t_start + w;
                 const float* y = G.tgt + (size_t)r * G.T;
@@ -27,9 +28,11 @@ __global__ void lane_stage_kernel(const LaneGroup* __restrict__ groups, int n_gr
                     tp[c2 * 32] = make_float2(v0, v1);
                 }
                 rw[G.rw_off + p] = (int32_t)(((uint32_t)r << 16) | (uint32_t)w);
+                if ((p & 31) == 0) ckey[G.ck_off + (p >> 5)] = __ldg(y + t - 1);
             } else {
                 for (int c2 = 0; c2 < DA2; ++c2) tp[c2 * 32] = make_float2(f_inf(), f_inf());
                 rw[G.rw_off + p] = 0;
+                if ((p & 31) == 0) ckey[G.ck_off + (p >> 5)] = f_inf();
             }
         }
     }
@@ -79,12 +82,12 @@ cudaError_t launch_lanes(int d, int ks, const BatchArgs& a, int grid, cudaStream
 }
 
 cudaError_t launch_lane_stage(const LaneGroup* groups, int n_groups, int max_np, const int32_t* sorted_idx,
-                              float2* tpart, int32_t* lane_rw, const LaneXBlock* xblocks, int n_xblocks,
-                              int64_t max_x, float* lane_x, int32_t* flags, cudaStream_t s) {
+                              float2* tpart, int32_t* lane_rw, float* lane_ckey, const LaneXBlock* xblocks,
+                              int n_xblocks, int64_t max_x, float* lane_x, int32_t* flags, cudaStream_t s) {
     if (n_groups <= 0) return cudaSuccess;
     const int threads = 256;
     const dim3 grid((unsigned)std::min(64, (max_np + threads - 1) / threads), (unsigned)std::min(n_groups, 65535));
-    lane_stage_kernel<<<grid, threads, 0, s>>>(groups, n_groups, sorted_idx, tpart, lane_rw);
+    lane_stage_kernel<<<grid, threads, 0, s>>>(groups, n_groups, sorted_idx, tpart, lane_rw, lane_ckey);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || n_xblocks <= 0) return e;
     const dim3 gx((unsigned)std::min<int64_t>(1024, (max_x + threads - 1) / threads),

@@ -209,3 +209,29 @@ def test_lanes_are_deterministic_and_replay(te_handle):
     te.te_set_sharing(te_handle, te.SHARE_AUTO)
     for key in a:
         assert torch.equal(a[key], b[key])
+
+
+@pytest.mark.parametrize("d,ties,mode", [(3, False, 3), (5, False, 1), (4, True, 3), (2, True, 3)])
+def test_strips_equal_unshared_and_oracle(te_handle, d, ties, mode):
+    """Groups of 4,500 points (1,500 trials x window 3) are cut into strips of 1,024 by a second
+    target coordinate, the last one ragged (404 points): the lane sweeps skip whole strips by the
+    second key. Radii and counts equal the unshared search (itself over strips) bit for bit and
+    the oracle on sampled estimates; many equal keys included."""
+    rng = np.random.default_rng(1000 + 10 * d + int(ties))
+    s = _series(rng, 1500, 40, d, 1, 3, 32, ties=ties)
+    insts = [I.Instance(0, 12, 3, p) for p in range(-1, 32)]  # 33 estimates
+    ds = te.to_device([s])
+    off, p0, _, _ = _run(te_handle, ds, insts, 4, te.SHARE_NONE)
+    on, p1, ops1, alg1 = _run(te_handle, ds, insts, 4, mode)
+    assert p0[0] == 0 and p1[0] == 33 and ops1 < alg1
+    assert torch.equal(off["counts"], on["counts"]) and torch.equal(off["eps"], on["eps"])
+    assert bool(((off["te"] - on["te"]).abs() <= off["err_bound"] + on["err_bound"]).all())
+    N = 4500
+    idx = [0, 17, 32]
+    o_te, o_counts, o_eps = oracle.te_batch([s], [insts[i] for i in idx], 4, want_counts=True)
+    eps = on["eps"].cpu().numpy().reshape(33, N)
+    counts = on["counts"].cpu().numpy().reshape(33, 3 * N)
+    for j, i in enumerate(idx):
+        np.testing.assert_array_equal(eps[i], o_eps[j * N:(j + 1) * N])
+        np.testing.assert_array_equal(counts[i], o_counts[3 * j * N:3 * (j + 1) * N])
+    assert np.max(np.abs(on["te"].cpu().numpy()[idx] - o_te)) <= TOL
