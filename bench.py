@@ -52,6 +52,7 @@ WORKLOADS = {
     "c4": dict(cid=4, kw={}, desc="C4 uneven MEG-like batch: 20 pink-noise pairs x 30 t, N 50..10000, D 3..11"),
     "c5": dict(cid=5, kw={}, desc="C5 large ensemble: N=12000, D=11, 200 t x (1+200) = 40,200 estimates"),
     "c5-small": dict(cid=5, kw=dict(n_t=2, S=20), desc="C5 shapes, 2 time points x (1+20)"),
+    "c5-4t": dict(cid=5, kw=dict(n_t=4), desc="C5 shapes, 4 time points x (1+200) = 804 estimates"),
     "ar1-scan": dict(cid=None, kw={}, desc="AR(1) unidirectional scenario (Table 1): 50 trials x 3000 samples, "
                      "d=1, windows of 300 (N=15000, D=3) at 0.2/0.5/0.8/1.1 s, delay scan u=1..20, "
                      "500 surrogates each = 40,080 estimates, k=4"),
