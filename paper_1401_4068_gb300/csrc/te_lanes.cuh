@@ -439,7 +439,7 @@ __device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& 
 // + kLaneWarps, ... (a fixed assignment, so the partial sums are deterministic), and the CTA adds
 // its warps' per-lane sums in warp order into one partial per estimate and query block.
 template <int d, int KS>
-__global__ void __launch_bounds__(kLaneThreads, d <= 4 ? 4 : 3) lane_kernel(const BatchArgs a) {
+__global__ void __launch_bounds__(kLaneThreads, d <= 5 ? 4 : 3) lane_kernel(const BatchArgs a) {
     __shared__ double s_v[kLaneWarps][32], s_w[kLaneWarps][32];
     __shared__ int s_item;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
