@@ -251,7 +251,7 @@ __device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& 
     };
 
     pass1_begin(a);
-    unsigned vis1 = 0, pas1 = 0;
+    unsigned vis = 0, pas = 0;  // references visited / passed (both passes)
     float t[KS];
 #pragma unroll
     for (int s = 0; s < KS; ++s) t[s] = f_inf();
@@ -263,10 +263,10 @@ __device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& 
         lane_diff<d>(r, tq, v);
         const float dT = absmax_range<0, 2 * DA2 - 1>(v);
         unsigned ball = __ballot_sync(0xffffffffu, dT < thr);
-        vis1 += min(32, N - (ch << 5));
+        vis += min(32, N - (ch << 5));
         if (ball) {
             const int xo = lane_xoff((uint32_t)rwv, ncols32);
-            pas1 += __popc(ball);
+            pas += __popc(ball);
             lane_push_refs<d, KS, lane_round<d>()>(ball, dT, xo, xlq, tau32, xq, t);
         }
         thr = lanes_max(mv ? t[KS - 1] : 0.0f);
@@ -345,23 +345,22 @@ __device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& 
     }
     const float e = topk_select(t, a.k);
     const float emax = lanes_max(mv ? e : 0.0f);
-    pass1_end(a, (unsigned long long)vis1 * nv);
+    pass1_end(a, (unsigned long long)vis * nv);
 
     // ---- pass 2: the chunks of the window of the largest eps (without strips inside those pass 1
     // visited; with strips, in every strip whose second-key range meets the window)
     const float lb = __fsub_rd(keyq, emax), rb = __fadd_ru(keyq, emax);
     float cz = 0.0f, cyz = 0.0f, cxz = 0.0f;
-    unsigned vis2 = 0, pas2 = 0;
     auto scan2 = [&](const float2 (&r)[DA2], int32_t rwv, int ch) {
         float v[2 * DA2];
         lane_diff<d>(r, tq, v);
         const float bv = absmax_range<1, 2 * DA2 - 1>(v);  // y- (and the repeated coordinate 1)
         const float ayz = fabsf(v[0]);                     // y_t (joined with b per reference)
         unsigned ball = __ballot_sync(0xffffffffu, bv < emax);
-        vis2 += min(32, N - (ch << 5));
+        vis += min(32, N - (ch << 5));
         if (ball) {
             const int xo = lane_xoff((uint32_t)rwv, ncols32);
-            pas2 += __popc(ball);
+            pas += __popc(ball);
             lane_count_refs<d, lane_round<d>()>(ball, bv, ayz, xo, xlq, tau32, xq, e, cz, cyz, cxz);
         }
     };
@@ -424,10 +423,9 @@ __device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& 
         // ops) runs once per reference for all lanes, the source part (2 d) only for references
         // that passed the shared test
         constexpr int D = 1 + 2 * d;
-        const unsigned long long vis = (unsigned long long)vis1 + vis2, pas = (unsigned long long)pas1 + pas2;
-        const unsigned long long pairs = vis * nv;
+        const unsigned long long pairs = (unsigned long long)vis * nv;
         const unsigned long long alg = pairs * 2ull * D;
-        const unsigned long long run = vis * 2ull * (1 + d) + pas * nv * 2ull * d;
+        const unsigned long long run = (unsigned long long)vis * 2ull * (1 + d) + (unsigned long long)pas * nv * 2ull * d;
         work_add(0, pairs);
         work_add(1, alg);
         work_add(2, alg > run ? alg - run : 0ull);
@@ -442,6 +440,7 @@ template <int d, int KS>
 __global__ void __launch_bounds__(kLaneThreads, d <= 5 ? 4 : 3) lane_kernel(const BatchArgs a) {
     __shared__ double s_v[kLaneWarps][32], s_w[kLaneWarps][32];
     __shared__ int s_item;
+    __shared__ LaneGroup s_group;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     work_reset();
     for (;;) {
@@ -451,7 +450,11 @@ __global__ void __launch_bounds__(kLaneThreads, d <= 5 ? 4 : 3) lane_kernel(cons
         const int ticket = s_item;
         if (ticket >= a.n_items) break;
         const LaneItem it = a.litems[a.item_base + ticket];
-        const LaneGroup G = a.lgroups[it.group];
+        // the item's group descriptor stays in shared memory (read where used, not held in
+        // registers through the sweeps)
+        if (threadIdx.x == 0) s_group = a.lgroups[it.group];
+        __syncthreads();
+        const LaneGroup& G = s_group;
         const int mi = it.mblock * 32 + lane;
         const bool mv = mi < G.n_mem;
         const InstDesc& J = a.insts[__ldg(a.lane_members + G.mem_off + min(mi, G.n_mem - 1))];
