@@ -34,10 +34,10 @@ constexpr int kSmemCapBytes = 64 * 1024;  // reference tile budget of the batche
 constexpr int kSweepSmemMaxBytes = 160 * 1024;  // sweep mode: room for whole query blocks per tile
 constexpr int64_t kResidentMaxBytes = 200 * 1024;  // sweep mode: whole instances in shared memory
 // device word array: [0] batched-kernel queue, [1] flags, [2..3] bundle-kernel queues, one lane-kernel
-// queue per d (kLaneMinD .. kLaneMaxD), then one queue per instance for per-instance launches
+// queue per (d, delay class) slot, then one queue per instance for per-instance launches
 constexpr int kWordLaneQueue = 4;
 constexpr int64_t kLaneXMaxBytes = (int64_t)16 << 30;  // member-minor source arrays of the lane kernel
-constexpr int kWordPerInstance = kWordLaneQueue + te::kLaneMaxD - te::kLaneMinD + 1;
+constexpr int kWordPerInstance = kWordLaneQueue + te::kLaneSlots;
 
 thread_local std::string g_create_error;  // per host thread: concurrent te_create calls do not race
 
@@ -127,7 +127,8 @@ struct Plan {
     int bd = 0, bgrid = 0, tgrid = 0, n_bundled = 0, n_bres = 0;
     size_t bsmem = 0, tsmem = 0;   // dynamic shared memory of the resident / tiled bundle launches
     // lane kernel (one estimate per lane): groups, their members, work items ordered by d
-    // (items of d: litems[lane_begin[d] .. lane_begin[d + 1] - 1]) and the grid per d
+    // and delay class (items of slot s = (d - kLaneMinD) * kLaneTauClasses + class:
+    // litems[lane_begin[s] .. lane_begin[s + 1] - 1]) and the grid per slot
     std::vector<te::LaneGroup> lgroups;
     std::vector<te::LaneItem> litems;
     std::vector<int32_t> lmembers;
@@ -137,8 +138,8 @@ struct Plan {
     std::vector<te::LaneXBlock> xblocks;
     int64_t x_total = 0, x_max = 0;  // floats of all / the largest member-minor source array
     int lane_max_np = 0;
-    int lane_begin[te::kLaneMaxD + 2] = {0};
-    int lane_grid[te::kLaneMaxD + 1] = {0};
+    int lane_begin[te::kLaneSlots + 1] = {0};
+    int lane_grid[te::kLaneSlots] = {0};
     int n_lane = 0;                // estimates on the lane kernel
     uint64_t table_hash = 0;  // of the device tables (instances, items, bundles): part of the graph key
 };
@@ -577,17 +578,18 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
             P->x_total = xtotal;
             P->x_max = xmax;
         }
-        for (int d = te::kLaneMinD; d <= te::kLaneMaxD; ++d) {
-            P->lane_begin[d] = (int)P->litems.size();
+        for (int slot = 0; slot < te::kLaneSlots; ++slot) {
+            const int d = te::kLaneMinD + slot / te::kLaneTauClasses, tc = slot % te::kLaneTauClasses;
+            P->lane_begin[slot] = (int)P->litems.size();
             for (int g = 0; g < (int)P->lgroups.size(); ++g) {
                 const te::LaneGroup& G = P->lgroups[g];
-                if (G.d != d) continue;
+                if (G.d != d || te::lane_tau_class(G.tau) != tc) continue;
                 for (int mb = 0; mb * 32 < G.n_mem; ++mb)
                     for (int q0 = 0; q0 < G.N; q0 += te::kLaneQB)
                         P->litems.push_back(te::LaneItem{g, mb, q0, cand_xb[g][mb]});
             }
         }
-        P->lane_begin[te::kLaneMaxD + 1] = (int)P->litems.size();
+        P->lane_begin[te::kLaneSlots] = (int)P->litems.size();
     }
     // target-part sharing: estimates with one target part (target series, repetitions, window
     // start, window, d, tau) form bundles of up to kBundleMax (no bundle of one), processed by the
@@ -838,16 +840,17 @@ te_status build_plan(te_handle* h, const te_series* series, int n_series, const 
         if (bper < 1) return h->fail(TE_ENOTIMPL, "bundle kernel does not fit: smem=%zu", smem);
         (tiled ? P->tgrid : P->bgrid) = (int)std::min<int64_t>((int64_t)bper * h->sm_count, n);
     }
-    for (int d = te::kLaneMinD; d <= te::kLaneMaxD; ++d) {
-        const int n = P->lane_begin[d + 1] - P->lane_begin[d];
+    for (int slot = 0; slot < te::kLaneSlots; ++slot) {
+        const int d = te::kLaneMinD + slot / te::kLaneTauClasses, tc = slot % te::kLaneTauClasses;
+        const int n = P->lane_begin[slot + 1] - P->lane_begin[slot];
         if (n <= 0) continue;
-        const void* lf = te::lane_kernel_ptr(d, ks);
-        if (!lf) return h->fail(TE_ENOTIMPL, "no lane kernel for d=%d ks=%d", d, ks);
+        const void* lf = te::lane_kernel_ptr(d, ks, tc);
+        if (!lf) return h->fail(TE_ENOTIMPL, "no lane kernel for d=%d ks=%d delay class %d", d, ks, tc);
         int lper = 0;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lper, lf, te::kLaneThreads, 0)) != cudaSuccess)
             return h->cuda_fail(e, "occupancy query (lanes)");
         if (lper < 1) return h->fail(TE_ENOTIMPL, "lane kernel does not fit");
-        P->lane_grid[d] = (int)std::min<int64_t>((int64_t)lper * h->sm_count, n);
+        P->lane_grid[slot] = (int)std::min<int64_t>((int64_t)lper * h->sm_count, n);
     }
     uint64_t th = 1469598103934665603ull;
     th = fnv(th, P->insts.data(), P->insts.size() * sizeof(InstDesc));
@@ -1094,10 +1097,9 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
     const int cfg[] = {k, P.threads, P.grid, P.smem_floats, P.var.dlo, P.var.dhi, P.var.ks, P.var.qpt,
                        P.var.warp_only ? 1 : 0,
                        n_groups, S, h->profiling ? 1 : 0, n_inst, P.var.sweep ? 1 : 0, P.bd, P.bgrid,
-                       (int)P.bsmem, P.tgrid, (int)P.tsmem, P.n_bres, P.n_lane, P.lane_max_np,
-                       P.lane_grid[2], P.lane_grid[3], P.lane_grid[4], P.lane_grid[5], P.lane_grid[6],
-                       P.lane_grid[7], P.lane_grid[8]};
+                       (int)P.bsmem, P.tgrid, (int)P.tsmem, P.n_bres, P.n_lane, P.lane_max_np};
     key = fnv(key, cfg, sizeof cfg);
+    key = fnv(key, P.lane_grid, sizeof P.lane_grid);
     const bool replay = !h->per_instance && h->graph_exec && h->graph_key == key &&
                         h->graph_gen == h->workspace_gen;
     if (h->per_instance) return run_per_instance(h, P, n_inst, k, te_dst, err, counts, eps, n_groups, S,
@@ -1132,14 +1134,15 @@ te_status run_batched(te_handle* h, const Plan& P, const te_series* series, int 
         }
         // an event recorded during capture becomes a graph node only with cudaEventRecordExternal
         if (ce == cudaSuccess && h->profiling) ce = cudaEventRecordWithFlags(h->ev0, h->cap_stream, cudaEventRecordExternal);
-        for (int d = te::kLaneMinD; d <= te::kLaneMaxD && ce == cudaSuccess; ++d) {
-            const int n = P.lane_begin[d + 1] - P.lane_begin[d];
+        for (int slot = 0; slot < te::kLaneSlots && ce == cudaSuccess; ++slot) {
+            const int n = P.lane_begin[slot + 1] - P.lane_begin[slot];
             if (n <= 0) continue;
             BatchArgs al = a;
-            al.item_base = P.lane_begin[d];
+            al.item_base = P.lane_begin[slot];
             al.n_items = n;
-            al.queue = h->d_words.p + kWordLaneQueue + (d - te::kLaneMinD);
-            ce = te::launch_lanes(d, P.var.ks, al, P.lane_grid[d], h->cap_stream);
+            al.queue = h->d_words.p + kWordLaneQueue + slot;
+            ce = te::launch_lanes(te::kLaneMinD + slot / te::kLaneTauClasses, P.var.ks, slot % te::kLaneTauClasses, al,
+                                  P.lane_grid[slot], h->cap_stream);
             ++launches;
         }
         for (int tiled = 0; tiled < 2 && ce == cudaSuccess; ++tiled) {

@@ -201,11 +201,20 @@ constexpr int kBundleQ = 1;         // queries per thread
 constexpr int kBundleThreads = 256;
 const void* bundle_kernel_ptr(int d, int ks, bool tiled);
 cudaError_t launch_bundle(int d, int ks, bool tiled, const BatchArgs& a, int grid, size_t smem, cudaStream_t s);
-// ---- the lane kernel (te_lanes_*.cu): one estimate per lane, d = kLaneMinD .. kLaneMaxD, k <= 4 ----
-const void* lane_kernel_ptr(int d, int ks);
-const void* lane_ptr_lo(int d, int ks);
-const void* lane_ptr_hi(int d, int ks);
-cudaError_t launch_lanes(int d, int ks, const BatchArgs& a, int grid, cudaStream_t s);
+// ---- the lane kernel (te_lanes*.cu): one estimate per lane, d = kLaneMinD .. kLaneMaxD, k <= 4, ----
+// ---- one instantiation per delay class (tau = 1, 2, 3 compiled in; class 0: any tau) ----
+constexpr int kLaneTauClasses = 4;
+constexpr int kLaneSlots = (kLaneMaxD - kLaneMinD + 1) * kLaneTauClasses;  // (d, delay class) pairs
+inline int lane_tau_class(int tau) { return tau >= 1 && tau < kLaneTauClasses ? tau : 0; }
+const void* lane_kernel_ptr(int d, int ks, int tc);
+const void* lane_ptr_d2(int ks, int tc);
+const void* lane_ptr_d3(int ks, int tc);
+const void* lane_ptr_d4(int ks, int tc);
+const void* lane_ptr_d5(int ks, int tc);
+const void* lane_ptr_d6(int ks, int tc);
+const void* lane_ptr_d7(int ks, int tc);
+const void* lane_ptr_d8(int ks, int tc);
+cudaError_t launch_lanes(int d, int ks, int tc, const BatchArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_lane_stage(const LaneGroup* groups, int n_groups, int max_np, const int32_t* sorted_idx,
                               float2* tpart, int32_t* lane_rw, float* lane_ckey, const LaneXBlock* xblocks,
                               int n_xblocks, int64_t max_x, float* lane_x, int32_t* flags, cudaStream_t s);

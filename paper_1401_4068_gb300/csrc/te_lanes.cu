@@ -1,4 +1,5 @@
-// Instantiations of the lane kernel (te_lanes.cuh) for d = 2 .. 4, k <= 4, and its pre-pass.
+// The lane kernel's pre-passes (sorted target parts, member-minor source arrays) and launchers;
+// its instantiations are in te_lanes_d2.cu .. te_lanes_d8.cu (one embedding dimension each).
 #include <algorithm>
 
 #include "te_lanes.cuh"
@@ -62,20 +63,21 @@ __global__ void lane_x_kernel(const LaneXBlock* __restrict__ blocks, int n_block
     }
 }
 
-const void* lane_ptr_lo(int d, int ks) {
-    if (ks != 5) return nullptr;
+const void* lane_kernel_ptr(int d, int ks, int tc) {
     switch (d) {
-        case 2: return (const void*)lane_kernel<2, 5>;
-        case 3: return (const void*)lane_kernel<3, 5>;
-        case 4: return (const void*)lane_kernel<4, 5>;
+        case 2: return lane_ptr_d2(ks, tc);
+        case 3: return lane_ptr_d3(ks, tc);
+        case 4: return lane_ptr_d4(ks, tc);
+        case 5: return lane_ptr_d5(ks, tc);
+        case 6: return lane_ptr_d6(ks, tc);
+        case 7: return lane_ptr_d7(ks, tc);
+        case 8: return lane_ptr_d8(ks, tc);
         default: return nullptr;
     }
 }
 
-const void* lane_kernel_ptr(int d, int ks) { return d <= 4 ? lane_ptr_lo(d, ks) : lane_ptr_hi(d, ks); }
-
-cudaError_t launch_lanes(int d, int ks, const BatchArgs& a, int grid, cudaStream_t s) {
-    const void* fn = lane_kernel_ptr(d, ks);
+cudaError_t launch_lanes(int d, int ks, int tc, const BatchArgs& a, int grid, cudaStream_t s) {
+    const void* fn = lane_kernel_ptr(d, ks, tc);
     if (!fn) return cudaErrorInvalidDeviceFunction;
     void* args[] = {const_cast<BatchArgs*>(&a)};
     return cudaLaunchKernel(fn, dim3(grid), dim3(kLaneThreads), args, 0, s);

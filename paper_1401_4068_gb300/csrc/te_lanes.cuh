@@ -209,7 +209,7 @@ __device__ __forceinline__ void lane_count_refs(unsigned ball, float bv, float a
     }
 }
 
-template <int d, int KS>
+template <int d, int KS, int TAU>
 __device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& G, const float* __restrict__ xlq,
                                            int ncols32, bool mv, unsigned nv, int p, FF& acc, float& acc_abs,
                                            const int64_t pt_off) {
@@ -225,7 +225,9 @@ __device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& 
     const float* ckl = a.lane_ckey + G.ck_off + lane;
     const int32_t* spos = a.strip_pos + G.strip_off;
     const float* sk2 = a.strip_k2 + 2 * G.strip_off;
-    const int tau32 = G.tau * 32;
+    // the embedding delay in floats of the member-minor arrays: a constant for TAU = 1, 2, 3 (the
+    // source coordinates of a point are then at immediate offsets), read at run time for TAU = 0
+    const int tau32 = TAU > 0 ? TAU * 32 : G.tau * 32;
 
     // the query (uniform): target coordinates, key and second key; the lane's source part
     const int pc = p >> 5;
@@ -437,7 +439,7 @@ __device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& 
 // block of kLaneQB sorted query positions) from the queue; warp w takes positions q0 + w, q0 + w
 // + kLaneWarps, ... (a fixed assignment, so the partial sums are deterministic), and the CTA adds
 // its warps' per-lane sums in warp order into one partial per estimate and query block.
-template <int d, int KS>
+template <int d, int KS, int TAU>
 __global__ void __launch_bounds__(kLaneThreads, d <= 5 ? 4 : 3) lane_kernel(const BatchArgs a) {
     __shared__ double s_v[kLaneWarps][32], s_w[kLaneWarps][32];
     __shared__ int s_item;
@@ -470,7 +472,7 @@ __global__ void __launch_bounds__(kLaneThreads, d <= 5 ? 4 : 3) lane_kernel(cons
         float acc_abs = 0.0f;
         const int qend = min(it.q0 + kLaneQB, G.N);
         for (int p = it.q0 + warp; p < qend; p += kLaneWarps)
-            lane_query<d, KS>(a, G, xlq, ncols32, mv, nv, p, acc, acc_abs, pt_off);
+            lane_query<d, KS, TAU>(a, G, xlq, ncols32, mv, nv, p, acc, acc_abs, pt_off);
         s_v[warp][lane] = (double)acc.hi + (double)acc.lo;
         s_w[warp][lane] = (double)acc_abs;
         __syncthreads();
@@ -487,6 +489,19 @@ __global__ void __launch_bounds__(kLaneThreads, d <= 5 ? 4 : 3) lane_kernel(cons
         }
     }
     work_flush(a);
+}
+
+// The instantiation for embedding dimension d, k <= 4 (ks = 5) and delay class tc (1, 2, 3: that
+// tau compiled in; 0: any tau read at run time).
+template <int d>
+const void* lane_kernel_select(int ks, int tc) {
+    if (ks != 5) return nullptr;
+    switch (tc) {
+        case 1: return (const void*)lane_kernel<d, 5, 1>;
+        case 2: return (const void*)lane_kernel<d, 5, 2>;
+        case 3: return (const void*)lane_kernel<d, 5, 3>;
+        default: return (const void*)lane_kernel<d, 5, 0>;
+    }
 }
 
 }  // namespace te

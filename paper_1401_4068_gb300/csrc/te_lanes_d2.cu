@@ -1,0 +1,8 @@
+// Instantiations of the lane kernel (te_lanes.cuh) for d = 2, k <= 4, every delay class.
+#include "te_lanes.cuh"
+
+namespace te {
+
+const void* lane_ptr_d2(int ks, int tc) { return lane_kernel_select<2>(ks, tc); }
+
+}  // namespace te

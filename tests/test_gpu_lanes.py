@@ -235,3 +235,14 @@ def test_strips_equal_unshared_and_oracle(te_handle, d, ties, mode):
         np.testing.assert_array_equal(eps[i], o_eps[j * N:(j + 1) * N])
         np.testing.assert_array_equal(counts[i], o_counts[3 * j * N:3 * (j + 1) * N])
     assert np.max(np.abs(on["te"].cpu().numpy()[idx] - o_te)) <= TOL
+
+
+@pytest.mark.parametrize("tau", [2, 3, 4])
+def test_every_delay_class(te_handle, tau):
+    """tau = 1, 2, 3 are compiled into the lane kernel, any other tau is read at run time: each
+    class equals the unshared search and the oracle."""
+    rng = np.random.default_rng(1100 + tau)
+    s = _series(rng, 45, 80, 3, tau, 3, 11)
+    t0 = 3 + 2 * tau + 4
+    insts = [I.Instance(0, t0, 3, p) for p in range(-1, 11)]
+    _check_against_unshared_and_oracle(te_handle, [s], insts, 4, 12)
