@@ -260,6 +260,7 @@ def cpu_baseline(w, seconds: float):
 
 # ---------------------------------------------------------------------------------- ours
 PATH_KERNELS = ("lane_kernel", "bundle_kernel", "batched_kernel")  # te_last_paths order
+SHARING = {"none": 0, "auto": 1, "bundles": 2, "lanes": 3}  # te_set_sharing modes
 
 
 def make_runner(te, torch, h, w, dev, units=None):
@@ -334,7 +335,8 @@ def bench_ours(args):
     ds = te.to_device(w.series, dev)
     te.te_set_profiling(h, True)
     te.te_set_search(h, not args.exhaustive)
-    te.te_set_sharing(h, te.SHARE_NONE if args.no_sharing else te.SHARE_AUTO)
+    share = te.SHARE_NONE if args.no_sharing else SHARING[args.sharing]
+    te.te_set_sharing(h, share)
 
     # strong scaling (default with several ranks): each rank takes a cost-balanced share of the
     # units and the per-unit results are all-gathered; weak: every rank runs the whole workload
@@ -538,7 +540,7 @@ def bench_ours(args):
             wsub = I.Workload(w.name, w.series, w.instances[: args.per_launch_instances], w.k)
         sub_step, sub_outs, _ = make_runner(te, torch, h, wsub, dev)
         arms = (("per_instance_launch", True, te.SHARE_NONE), ("batched_same_kernel", False, te.SHARE_NONE),
-                ("batched_default", False, te.SHARE_NONE if args.no_sharing else te.SHARE_AUTO))
+                ("batched_default", False, share))
         pe_sub = 2 * pair_evals(wsub)
         n_sub = len(wsub.instances) * _scan_factor(wsub)
         per = {"instances": n_sub}
@@ -560,7 +562,7 @@ def bench_ours(args):
                          "kernel_path": {k: v for k, v in zip(PATH_KERNELS, pth) if v},
                          "launch": "one per estimate" if per_inst else "one persistent launch (CUDA graph)"}
         te.te_set_batching(h, False)
-        te.te_set_sharing(h, te.SHARE_NONE if args.no_sharing else te.SHARE_AUTO)
+        te.te_set_sharing(h, share)
         per["batched_vs_per_launch"] = round(per["per_instance_launch"]["ms"] / per["batched_same_kernel"]["ms"], 2)
         per["default_vs_per_launch"] = round(per["per_instance_launch"]["ms"] / per["batched_default"]["ms"], 2)
 
@@ -654,6 +656,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--exhaustive", action="store_true", help="exhaustive search instead of the sorted sweep")
     ap.add_argument("--no-sharing", action="store_true", help="no target-part sharing across estimates")
+    ap.add_argument("--sharing", choices=sorted(SHARING), default="auto",
+                    help="target-part sharing: auto (lanes for large groups, bundles for small), lanes, bundles, none")
     ap.add_argument("--shape", default=None, help="fixed launch shape THREADSxQPT instead of autotuning")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

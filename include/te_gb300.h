@@ -227,7 +227,7 @@ te_status te_last_work(te_handle* h, uint64_t* pairs, uint64_t* ops, int32_t* sw
  * distance and count once for several estimates. The paper computes each surrogate separately;
  * this is exact because max is exact: each estimate sees the same FP32 differences the unshared
  * search computes.
- *   enable = 1 (default): groups of at least 32 such estimates with d = 4..8 run one estimate per
+ *   enable = 1 (default): groups of at least 32 such estimates with d = 3..8 run one estimate per
  *     lane (a warp takes one query point for 32 estimates; a reference whose target-part distance
  *     already reaches every lane's current radius is skipped for all 32 before any source
  *     coordinate is read); other groups of two or more with d <= 5 run in bundles of up to 3

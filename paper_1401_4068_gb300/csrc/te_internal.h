@@ -117,10 +117,10 @@ constexpr int kLaneThreads = 32 * kLaneWarps;
 constexpr int kLaneQB = 256;         // sorted query positions per work item (one partial sum each)
 constexpr int kLaneMinMembers = 8;   // smallest group the lane kernel takes (sharing mode 3)
 // sharing mode 1 (default): the lane kernel for groups of at least kLaneAutoMembers estimates
-// with d >= kLaneAutoMinD, where it measured faster than bundles or the unshared kernel (C5-
-// shaped and Lorenz delay scans: yes; C3-shaped d = 3 and the 16-estimate 17-D benchmark chunk:
+// with d >= kLaneAutoMinD, where it measured faster than bundles or the unshared kernel (C5- and
+// C3-shaped surrogate tests and the Lorenz delay scan: yes; the 16-estimate 17-D benchmark chunk:
 // no)
-constexpr int kLaneAutoMembers = 32, kLaneAutoMinD = 4;
+constexpr int kLaneAutoMembers = 32, kLaneAutoMinD = 3;
 constexpr int kLaneMinD = 2, kLaneMaxD = 8;
 
 // Bits of the device flag word.

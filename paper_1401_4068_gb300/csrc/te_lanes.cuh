@@ -95,11 +95,12 @@ __device__ __forceinline__ void lane_diff(const float2 (&r)[(d + 2) / 2], const 
 }
 
 // Passing references evaluated per round of a lane sweep (their loads in flight together), chosen
-// per embedding dimension by measurement on GB300: 4 for d <= 3 (C3 shapes), an explicitly written
-// pair (0) from d = 4 on (the Lorenz delay scan, d = 4: 625 ms against 849 ms with the generic pair
-// and 4 per round; C5 shapes, d = 5: 307.7 ms against 310.3 ms generic and 431 ms with 4).
+// by measurement on GB300: an explicitly written pair (0) from d = 3 on (C3 shapes, d = 3: 42.4 ms
+// against 44.6 ms with 4 per round; the Lorenz delay scan, d = 4: 625 ms against 849 ms with a
+// generic pair loop; C5 shapes, d = 5: 307.7 ms against 310.3 ms generic and 431 ms with 4), 4 per
+// round for d = 2.
 template <int d>
-__host__ __device__ constexpr int lane_round() { return d <= 3 ? 4 : 0; }
+__host__ __device__ constexpr int lane_round() { return d <= 2 ? 4 : 0; }
 
 // pass 1: push the joint distances of the references in `ball` (their dT and source offsets xo
 // live in the lanes named by the bits) into the lane's top-k list

@@ -1,5 +1,5 @@
 """One estimate per lane (the lane kernel, forced here with te.SHARE_LANES; by default it takes
-groups of at least 32 estimates with d >= 4): a group of at least 8 estimates that share y_t and y-
+groups of at least 32 estimates with d >= 3): a group of at least 8 estimates that share y_t and y-
 (the original and its trial-shuffled surrogates, every scanned delay u) runs with a warp per
 query point and one estimate per lane; a reference whose target-part distance already reaches
 every lane's radius is skipped for all of them. Per-point radii and counts must equal the
@@ -179,19 +179,21 @@ def test_bad_permutation_entry_in_lanes_is_flagged(te_handle):
 
 
 def test_default_rule_takes_large_groups_of_wide_estimates(te_handle):
-    """By default the lane kernel takes groups of 32 or more estimates with d >= 4 only."""
+    """By default the lane kernel takes groups of 32 or more estimates with d >= 3 only."""
     rng = np.random.default_rng(950)
     s4 = _series(rng, 40, 60, 4, 1, 2, 40)
     s3 = I.Series(s4.src, s4.tgt, d=3, tau=1, u=2, perms=s4.perms)
-    # 41 estimates with d = 4: lanes; the rest share in bundles of one d per batch, the d with
-    # the most of them (41 with d = 3 against 31 with d = 4), so the 31 run unshared
+    # 41 estimates with d = 4 and 41 with d = 3: lanes; the group of 31 (d = 4): bundles; a
+    # group of 3 with d = 2: bundles are of one d per batch (the d with most), so it runs unshared
+    s2 = I.Series(s4.src, s4.tgt, d=2, tau=1, u=2, perms=s4.perms)
     insts = ([I.Instance(0, 20, 2, p) for p in range(-1, 40)] +
              [I.Instance(0, 30, 2, p) for p in range(-1, 30)] +
-             [I.Instance(1, 20, 2, p) for p in range(-1, 40)])
-    ds = te.to_device([s4, s3])
+             [I.Instance(1, 20, 2, p) for p in range(-1, 40)] +
+             [I.Instance(2, 25, 2, p) for p in range(-1, 2)])
+    ds = te.to_device([s4, s3, s2])
     on, paths, _, _ = _run(te_handle, ds, insts, 4, te.SHARE_AUTO)
-    assert paths == (41, 41, 31)
-    o_te, o_counts, o_eps = oracle.te_batch([s4, s3], insts, 4, want_counts=True)
+    assert paths == (82, 31, 3)
+    o_te, o_counts, o_eps = oracle.te_batch([s4, s3, s2], insts, 4, want_counts=True)
     np.testing.assert_array_equal(on["counts"].cpu().numpy(), o_counts)
     np.testing.assert_array_equal(on["eps"].cpu().numpy(), o_eps)
     assert np.max(np.abs(on["te"].cpu().numpy() - o_te)) <= TOL
