@@ -434,9 +434,9 @@ def bench_ours(args):
                                 "the device; pass 2 includes the digamma terms)"}
         for name, pp, cyc in (("pass1_knn", pass_pairs[0], pass_cycles[0]),
                               ("pass2_counts", pass_pairs[1], pass_cycles[1])):
-            share = cyc / sum(pass_cycles)
-            passes[name] = {"cycle_share": round(share, 4),
-                            "pair_evals_per_s": copies * (pe_step / 2) * args.steps / (total_ms * share / 1e3),
+            cyc_frac = cyc / sum(pass_cycles)
+            passes[name] = {"cycle_share": round(cyc_frac, 4),
+                            "pair_evals_per_s": copies * (pe_step / 2) * args.steps / (total_ms * cyc_frac / 1e3),
                             "pair_evals_executed_per_step": pp,
                             "executed_vs_algorithmic": round(pp / max(1.0, per_pass), 4)}
 
@@ -544,9 +544,9 @@ def bench_ours(args):
         pe_sub = 2 * pair_evals(wsub)
         n_sub = len(wsub.instances) * _scan_factor(wsub)
         per = {"instances": n_sub}
-        for name, per_inst, share in arms:
+        for name, per_inst, mode in arms:
             te.te_set_batching(h, per_inst)
-            te.te_set_sharing(h, share)
+            te.te_set_sharing(h, mode)
             sub_step(ds, sub_outs)
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -423,6 +423,8 @@ def te_set_sharing(h: Handle, mode):
     """Target-part sharing: 1 or True (default) = one estimate per lane for groups of at least 32
     estimates with one target part and d = 3..8, bundles of up to 3 for other groups; 3 = the lane
     kernel for every group of at least 8 with d = 2..8; 2 = bundles only; 0 or False = none."""
+    if not isinstance(mode, (bool, int)):
+        raise TypeError(f"te_set_sharing: mode must be an int or bool, got {type(mode).__name__}")
     h.check(h.lib.te_set_sharing(h.h, int(mode)))
 
 
