@@ -102,6 +102,29 @@ __device__ __forceinline__ void lane_diff(const float2 (&r)[(d + 2) / 2], const 
 template <int d>
 __host__ __device__ constexpr int lane_round() { return d <= 2 ? 4 : 0; }
 
+// insertion into the ascending top-KS list without a branch (a value >= t[KS - 1] leaves the
+// list unchanged through the min/max network)
+template <int KS>
+__device__ __forceinline__ void lane_topk_push(float (&t)[KS], float x) {
+#pragma unroll
+    for (int s = KS - 1; s > 0; --s) t[s] = fmaxf(t[s - 1], fminf(t[s], x));
+    t[0] = fminf(t[0], x);
+}
+
+// insertion of two values at once: with lo <= hi the pair in order, slot s of the merged list is
+// the smallest of t[s], max(lo, t[s - 1]) and max(hi, t[s - 2]) (a min/max network of depth 3)
+template <int KS>
+__device__ __forceinline__ void lane_topk_push2(float (&t)[KS], float x0, float x1) {
+    const float lo = fminf(x0, x1), hi = fmaxf(x0, x1);
+    float m[KS];
+    m[0] = fminf(t[0], lo);
+    if constexpr (KS > 1) m[1] = fminf(fminf(t[1], fmaxf(lo, t[0])), hi);
+#pragma unroll
+    for (int s = 2; s < KS; ++s) m[s] = fminf(fminf(t[s], fmaxf(lo, t[s - 1])), fmaxf(hi, t[s - 2]));
+#pragma unroll
+    for (int s = 0; s < KS; ++s) t[s] = m[s];
+}
+
 // pass 1: push the joint distances of the references in `ball` (their dT and source offsets xo
 // live in the lanes named by the bits) into the lane's top-k list
 template <int d, int KS, int RB>
@@ -124,8 +147,7 @@ __device__ __forceinline__ void lane_push_refs(unsigned ball, float dT, int xo, 
             lane_source<d>(xlq + xo1, tau32, x1);
             const float d0 = lane_join<d>(dT0, xq, x0);
             const float d1 = two ? lane_join<d>(dT1, xq, x1) : f_inf();
-            topk_push(t, d0);
-            topk_push(t, d1);
+            lane_topk_push2(t, d0, d1);
         }
     } else {
         while (ball) {
@@ -146,7 +168,7 @@ __device__ __forceinline__ void lane_push_refs(unsigned ball, float dT, int xo, 
             }
 #pragma unroll
             for (int b = 0; b < RB; ++b)  // a missing reference pushes +inf (no change)
-                topk_push(t, ok[b] ? lane_join<d>(dr[b], xq, xr[b]) : f_inf());
+                lane_topk_push(t, ok[b] ? lane_join<d>(dr[b], xq, xr[b]) : f_inf());
         }
     }
 }
@@ -223,9 +245,10 @@ __device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& 
     const float2* tpb = a.tpart + G.tp_off;  // uniform base; tpb + lane: this lane's column
     const float2* tpl = tpb + lane;
     const int32_t* rwl = a.lane_rw + G.rw_off + lane;
-    const float* ckl = a.lane_ckey + G.ck_off + lane;
-    const int32_t* spos = a.strip_pos + G.strip_off;
-    const float* sk2 = a.strip_k2 + 2 * G.strip_off;
+    // strip tables read through the group descriptor in shared memory where used (no pointers
+    // held in registers through the sweeps)
+    auto spos = [&](int s) { return __ldg(a.strip_pos + G.strip_off + s); };
+    auto sk2 = [&](int i) { return __ldg(a.strip_k2 + 2 * G.strip_off + i); };
     // the embedding delay in floats of the member-minor arrays: a constant for TAU = 1, 2, 3 (the
     // source coordinates of a point are then at immediate offsets), read at run time for TAU = 0
     const int tau32 = TAU > 0 ? TAU * 32 : G.tau * 32;
@@ -249,8 +272,8 @@ __device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& 
     // of the strip's chunk l; the window starts at the last chunk whose first key is <= lb.
     auto strip_start = [&](int s, float lb, float& fk, int& ce) {
         const int cs = s << 5;
-        ce = min(nch, (__ldg(spos + s + 1) + 31) >> 5);
-        fk = cs + lane < ce ? __ldg(ckl + cs) : f_inf();
+        ce = min(nch, (spos(s + 1) + 31) >> 5);
+        fk = cs + lane < ce ? __ldg(a.lane_ckey + G.ck_off + lane + cs) : f_inf();
         return cs + max(0, __popc(__ballot_sync(0xffffffffu, fk <= lb)) - 1);
     };
 
@@ -272,8 +295,8 @@ __device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& 
             const int xo = lane_xoff((uint32_t)rwv, ncols32);
             pas += __popc(ball);
             lane_push_refs<d, KS, lane_round<d>()>(ball, dT, xo, xlq, tau32, xq, t);
+            thr = lanes_max(mv ? t[KS - 1] : 0.0f);  // the lists change only here
         }
-        thr = lanes_max(mv ? t[KS - 1] : 0.0f);
     };
     // The sweeps load chunk ch + 1 (or ch - 1) before processing chunk ch, so its latency overlaps
     // the work on ch; the window test reads the key of a chunk's first (right) or last (left)
@@ -284,7 +307,7 @@ __device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& 
     int cs0 = 0, ce0 = nch;
     if (S > 1) {
         cs0 = pc & ~31;
-        ce0 = min(nch, (__ldg(spos + (pc >> 5) + 1) + 31) >> 5);
+        ce0 = min(nch, (spos((pc >> 5) + 1) + 31) >> 5);
     }
     int chl = pc, chr = pc;
     lane_load<d>(tpl + pc * CH, rwl + (pc << 5), cur, rwc);
@@ -324,11 +347,11 @@ __device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& 
                     else down = false;
                     continue;
                 }
-                if (side == 0 && !(__ldg(sk2 + 2 * s) < __fadd_ru(k2q, thr))) {
+                if (side == 0 && !(sk2(2 * s) < __fadd_ru(k2q, thr))) {
                     up = false;
                     continue;
                 }
-                if (side == 1 && !(__ldg(sk2 + 2 * s + 1) > __fsub_rd(k2q, thr))) {
+                if (side == 1 && !(sk2(2 * s + 1) > __fsub_rd(k2q, thr))) {
                     down = false;
                     continue;
                 }
@@ -371,8 +394,8 @@ __device__ __forceinline__ void lane_query(const BatchArgs& a, const LaneGroup& 
     if (S > 1) {
         const float lb2 = __fsub_rd(k2q, emax), rb2 = __fadd_ru(k2q, emax);
         for (int s = 0; s < S; ++s) {
-            if (!(__ldg(sk2 + 2 * s + 1) > lb2)) continue;  // strip entirely below the window
-            if (!(__ldg(sk2 + 2 * s) < rb2)) break;         // this and every later strip above it
+            if (!(sk2(2 * s + 1) > lb2)) continue;  // strip entirely below the window
+            if (!(sk2(2 * s) < rb2)) break;         // this and every later strip above it
             float fk;
             int ce;
             const int c0 = strip_start(s, lb, fk, ce);
