@@ -27,6 +27,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -108,15 +109,32 @@ def lane_ops(w):
                                      for i in w.instances)
 
 
-def kernel_source_hash() -> str:
-    """Hash of the device-code sources (every csrc file but the host-only C ABI layer)."""
-    h = hashlib.sha256()
+# the translation units that hold each search kernel (file-name prefixes under csrc/)
+KERNEL_UNITS = {"lane_kernel": ("te_lanes",), "batched_kernel": ("te_batched_d", "te_batched_mix"),
+                "bundle_kernel": ("te_bundle.cu",)}
+
+
+def kernel_source_hash(kernel: str) -> str:
+    """Hash of the device code a search kernel is built from: its translation units and every
+    project header they include, directly or not (a change elsewhere leaves it unchanged)."""
     csrc = os.path.join(ROOT, "paper_1401_4068_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f == "te_api.cu":
+    inc = os.path.join(ROOT, "include")
+    todo = sorted(f for f in os.listdir(csrc)
+                  if f.endswith(".cu") and f.startswith(KERNEL_UNITS[kernel]))
+    seen = {}
+    while todo:
+        f = todo.pop()
+        if f in seen:
             continue
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+        path = next((os.path.join(d, f) for d in (csrc, inc) if os.path.exists(os.path.join(d, f))), None)
+        if path is None:
+            continue
+        with open(path, "rb") as fh:
+            seen[f] = fh.read()
+        todo += re.findall(r'^\s*#include\s+"([^"]+)"', seen[f].decode(), flags=re.M)
+    h = hashlib.sha256()
+    for f in sorted(seen):
+        h.update(f.encode() + seen[f])
     return h.hexdigest()[:16]
 
 
@@ -196,7 +214,7 @@ def traffic_per_launch(w, kernel):
             prof = json.load(f)
     except (OSError, ValueError):
         return None
-    if prof.get("kernel_src_hash") != kernel_source_hash():
+    if kernel not in KERNEL_UNITS or prof.get("kernel_src_hash") != kernel_source_hash(kernel):
         return None
     shape = sorted({(w.n_points(i), w.joint_dim(i)) for i in w.instances})
     if [list(x) for x in shape] != prof.get("instance_shapes"):

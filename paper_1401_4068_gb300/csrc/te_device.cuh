@@ -31,6 +31,21 @@ __device__ __forceinline__ void topk_push(float (&t)[KS], float x) {
     }
 }
 
+// four candidates: one test of their minimum against the last slot guards the four insertions
+// (once the list has filled, most groups of four change nothing)
+template <int KS>
+__device__ __forceinline__ void topk_push4(float (&t)[KS], float m0, float m1, float m2, float m3) {
+    if (fminf(fminf(m0, m1), fminf(m2, m3)) < t[KS - 1]) {
+        const float v[4] = {m0, m1, m2, m3};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+#pragma unroll
+            for (int s = KS - 1; s > 0; --s) t[s] = fmaxf(t[s - 1], fminf(t[s], v[e]));
+            t[0] = fminf(t[0], v[e]);
+        }
+    }
+}
+
 // slot k of the ascending list (k is a runtime value < KS), written as the maximum of slots
 // 0..k so that the list stays in registers (a select on s == k is compiled as a dynamic index)
 template <int KS>
@@ -141,10 +156,8 @@ __device__ __forceinline__ void knn_step4(const u64 (&qq)[Q][D], const ulonglong
         for (int q = 0; q < Q; ++q) {
             float dx[D], dy[D], dz[D], dw[D];
             diff4<D>(qq[q], r, dx, dy, dz, dw);
-            topk_push(t[q], absmax_range<0, D - 1>(dx));
-            topk_push(t[q], absmax_range<0, D - 1>(dy));
-            topk_push(t[q], absmax_range<0, D - 1>(dz));
-            topk_push(t[q], absmax_range<0, D - 1>(dw));
+            topk_push4(t[q], absmax_range<0, D - 1>(dx), absmax_range<0, D - 1>(dy), absmax_range<0, D - 1>(dz),
+                       absmax_range<0, D - 1>(dw));
         }
     } else {
         float m[Q][4];
@@ -158,9 +171,7 @@ __device__ __forceinline__ void knn_step4(const u64 (&qq)[Q][D], const ulonglong
             m[q][3] = absmax_range<0, D - 1>(dw);
         }
 #pragma unroll
-        for (int q = 0; q < Q; ++q)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) topk_push(t[q], m[q][e]);
+        for (int q = 0; q < Q; ++q) topk_push4(t[q], m[q][0], m[q][1], m[q][2], m[q][3]);
     }
 }
 
