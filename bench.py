@@ -265,10 +265,11 @@ def cpu_baseline(w, seconds: float):
     n = max(threads, 8)
     idx = I.sample_instances(w, n, seed=11)
     pe, dt, m = run_oracle_sample(w, idx, threads)
-    if dt < seconds / 3:
-        scale = min(64.0, seconds / max(dt, 1e-3))
-        n2 = min(len(w.instances), int(n * scale))
-        idx = I.sample_instances(w, n2, seed=12)
+    for seed in (12, 13):  # resample, sized from the last sample's rate, until it fills the budget
+        if dt >= 0.8 * seconds or n >= len(w.instances):
+            break
+        n = min(len(w.instances), max(n + 1, int(n * min(64.0, seconds / max(dt, 1e-3)))))
+        idx = I.sample_instances(w, n, seed=seed)
         pe, dt, m = run_oracle_sample(w, idx, threads)
     return {"value": pe / dt, "unit": "pair-evals/s", "cores": threads, "kind": "oracle",
             "seconds": round(dt, 2), "te_estimates_per_s": m / dt,
@@ -677,7 +678,7 @@ def main():
     ap.add_argument("--sharing", choices=sorted(SHARING), default="auto",
                     help="target-part sharing: auto (lanes for large groups, bundles for small), lanes, bundles, none")
     ap.add_argument("--shape", default=None, help="fixed launch shape THREADSxQPT instead of autotuning")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-instances", type=int, default=32)
     args = ap.parse_args()
